@@ -1,0 +1,62 @@
+"""Nested potential at sampled cells by direct summation only (oracle).
+
+A second route to the same quantity as ``nested.solve``: every component
+potential that the assembly needs at the sampled cell (Eq. 14, or Eqs. 15 and
+B.1-B.2) is evaluated by the plain sum of Eq. 10 over the component's masses,
+with no Fourier transform.  The cost is O(samples * levels * 8 * N^3), so it can
+check a few cells of meshes far too large for the FFT oracle.
+
+Test infrastructure only; see the package docstring.
+"""
+import numpy as np
+
+from .convolution import direct_sum_at
+from .nested import Geometry, interp_coords, level_masses, restrict
+
+
+def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original"):
+    """Phi(Omega^n) at cells ``samples`` = iterable of (n, z, y, x)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    L = rho.shape[0]
+    geom = Geometry(L, N, dx0)
+    rho_r = restrict(rho, N)
+    full_M, hole_M = level_masses(rho_r, geom)
+    out = []
+    for (n, z, y, x) in samples:
+        cell = np.array([[z, y, x]], dtype=np.float64)
+        if method == "original" or n == L - 1:
+            val = direct_sum_at(full_M[n], geom.dx(n), G, cell)[0]
+        elif method == "dipole":
+            val = direct_sum_at(hole_M[n], geom.dx(n), G, cell)[0]
+            # doubled fine grid of level n+1: 2N cells spanning level n, fine
+            # block at [N/2, 3N/2).  The 2^3 fine cells inside coarse cell
+            # (z, y, x) sit at 2*(z,y,x) + {0,1}; in the fine block's own index
+            # lattice that is 2*(z,y,x) + {0,1} - N/2.
+            fine = []
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        fine.append([2 * z + dz - N // 2, 2 * y + dy - N // 2,
+                                     2 * x + dx - N // 2])
+            rho_fine_M = rho_r[n + 1] * geom.dx(n + 1) ** 3
+            val += direct_sum_at(rho_fine_M, geom.dx(n + 1), G, np.array(fine, float)).mean()
+        else:
+            raise ValueError("method must be 'original' or 'dipole'")
+        for k in range(n):
+            u = interp_coords(N, k, n)
+            pts, wts = [], []
+            for idx_axis, i in enumerate((z, y, x)):
+                i0 = int(np.floor(u[i]))
+                t = u[i] - i0
+                pts.append((i0, i0 + 1))
+                wts.append((1.0 - t, t))
+            corners, weights = [], []
+            for a in (0, 1):
+                for b in (0, 1):
+                    for c in (0, 1):
+                        corners.append([pts[0][a], pts[1][b], pts[2][c]])
+                        weights.append(wts[0][a] * wts[1][b] * wts[2][c])
+            vals = direct_sum_at(hole_M[k], geom.dx(k), G, np.array(corners, float))
+            val += float(np.dot(weights, vals))
+        out.append(val)
+    return np.array(out)

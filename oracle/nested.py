@@ -1,0 +1,200 @@
+"""Nested-mesh convolution method (oracle, float64): Sect. 4 and Sect. 7.
+
+Geometry (Sect. 2, Fig. 1): level m = 0 (coarsest) ... L-1 (finest), each N^3
+cells, level m of cell size dx_m = dx0 / 2^m and side N dx_m, all levels centred
+on the origin.  Cell centres: x_i = -N dx_m / 2 + (i + 1/2) dx_m.  Level m+1
+therefore occupies level-m cells [N/4, 3N/4) on every axis (the same offset as
+ib = N/4 + i/2 + 1 in Eqs. 3-6).  Arrays are indexed [level, z, y, x].
+
+Readings taken where the paper is silent (each listed in the design notes):
+* Coarse covered cells carry the restriction of the finer level (the mean of
+  the 2^3 children, swept finest -> coarsest), so the coarse grid sees the fine
+  mass (Sect. 4, Sect. 7 "projected from the fine to the coarse grid").  The
+  caller's coarse values there are ignored.
+* Cell mass M = rho(centre) * dx^3.
+* The interpolation of Fig. 6 (stripped from the source) is trilinear, from
+  level k straight to level n (no cascade through intermediate levels).
+* The "reduction" of the doubled fine grid to the coarse grid (Sect. 7) is the
+  mean of the 2^3 fine values in each coarse cell.
+* Eq. B.1 writes the coarser-level sum with superscript m = n; it is read as
+  m = k (the same sum as Eq. 14).
+
+Test infrastructure only; see the package docstring.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from .convolution import isolated_convolution
+from .green import green_spectrum
+
+
+@dataclass(frozen=True)
+class Geometry:
+    levels: int
+    N: int
+    dx0: float
+
+    def __post_init__(self):
+        if self.levels < 1:
+            raise ValueError("levels must be >= 1")
+        if self.N < 4 or self.N % 4 != 0:
+            raise ValueError("N must be a multiple of 4")
+
+    def dx(self, m):
+        return self.dx0 / (2.0 ** m)
+
+    def centres(self, m):
+        """Cell-centre coordinates of level m along one axis."""
+        dx = self.dx(m)
+        return -self.N * dx / 2.0 + (np.arange(self.N) + 0.5) * dx
+
+    @property
+    def covered(self):
+        """Half-open index range of level m covered by level m + 1."""
+        return self.N // 4, 3 * self.N // 4
+
+
+def restrict(rho, N):
+    """Replace each level's covered cells by the 2^3 mean of the finer level.
+
+    Swept from the finest level to the coarsest, so every covered coarse cell
+    holds the mean of the finest data below it and the total mass
+    sum_m sum_uncovered rho dx_m^3 is exactly that of the composite mesh.
+    """
+    rho = np.array(rho, dtype=np.float64, copy=True)
+    L = rho.shape[0]
+    a, b = N // 4, 3 * N // 4
+    h = N // 2
+    for m in range(L - 2, -1, -1):
+        child = rho[m + 1]
+        avg = child.reshape(h, 2, h, 2, h, 2).mean(axis=(1, 3, 5))
+        rho[m, a:b, a:b, a:b] = avg
+    return rho
+
+
+def level_masses(rho_restricted, geom):
+    """Full and hole mass arrays per level (Fig. 5).
+
+    full[m] = rho_m dx_m^3 on all N^3 cells; hole[m] = the same with the cells
+    covered by level m + 1 set to zero (Omega^m_hole); the finest level has no
+    hole grid (None).
+    """
+    L, N = geom.levels, geom.N
+    a, b = geom.covered
+    full, hole = [], []
+    for m in range(L):
+        M = rho_restricted[m] * geom.dx(m) ** 3
+        full.append(M)
+        if m < L - 1:
+            Mh = M.copy()
+            Mh[a:b, a:b, a:b] = 0.0
+            hole.append(Mh)
+        else:
+            hole.append(None)
+    return full, hole
+
+
+def interp_coords(N, k, n):
+    """Level-k fractional index of each level-n cell centre along one axis.
+
+    From the geometry above: u = (x_i^n - x_0^k) / dx_k
+      = N/2 - N/(2r) + (i + 1/2)/r - 1/2,   r = 2^(n-k).
+    Written in index space it is exact in binary floating point (dyadic).
+    """
+    r = 2.0 ** (n - k)
+    i = np.arange(N, dtype=np.float64)
+    return N / 2.0 - N / (2.0 * r) + (i + 0.5) / r - 0.5
+
+
+def trilinear_to_level(phi_k, N, k, n):
+    """Tensor-product linear interpolation of a level-k field to the level-n
+    cell centres (n > k), the tilde operator of Eq. 14 (Fig. 6)."""
+    u = interp_coords(N, k, n)
+    i0 = np.floor(u).astype(np.int64)
+    t = u - i0
+    if i0.min() < 0 or i0.max() + 1 > N - 1:
+        raise AssertionError("interpolation stencil leaves level k")
+    out = np.zeros((N, N, N))
+    for az in (0, 1):
+        wz = t if az else 1.0 - t
+        for ay in (0, 1):
+            wy = t if ay else 1.0 - t
+            for ax in (0, 1):
+                wx = t if ax else 1.0 - t
+                vals = phi_k[np.ix_(i0 + az, i0 + ay, i0 + ax)]
+                out += wz[:, None, None] * wy[None, :, None] * wx[None, None, :] * vals
+    return out
+
+
+def reduce_2x(fine):
+    """Mean of the 2^3 fine values in each coarse cell (the Sect. 7 reduction)."""
+    n = fine.shape[0] // 2
+    return fine.reshape(n, 2, n, 2, n, 2).mean(axis=(1, 3, 5))
+
+
+def solve_components(rho, N, dx0, G=1.0, method="original", want=("full", "hole")):
+    """Per-level component potentials of the decomposition.
+
+    Returns a dict with 'full' (Phi^m on Omega^m), 'hole' (Phi^m_hole on
+    Omega^m_hole, None for the finest level), 'dbl' (reduced Phi^{m+1}_dbl on
+    level m, pairwise-dipole method only) and 'rho' (restricted densities).
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    L = rho.shape[0]
+    geom = Geometry(L, N, dx0)
+    if rho.shape != (L, N, N, N):
+        raise ValueError("rho must be (levels, N, N, N)")
+    rho_r = restrict(rho, N)
+    full_M, hole_M = level_masses(rho_r, geom)
+    spec = green_spectrum(N)
+    out = {"rho": rho_r, "full": [None] * L, "hole": [None] * L, "dbl": [None] * L}
+    for m in range(L):
+        if "full" in want and (method == "original" or m == L - 1):
+            out["full"][m] = isolated_convolution(full_M[m], geom.dx(m), G, spec)
+        if hole_M[m] is not None:
+            out["hole"][m] = isolated_convolution(hole_M[m], geom.dx(m), G, spec)
+    if method == "dipole":
+        spec2 = green_spectrum(2 * N) if L > 1 else None
+        for n in range(L - 1):
+            out["dbl"][n] = reduce_2x(doubled_fine_potential(rho_r[n + 1], geom, n + 1, G, spec2))
+    elif method != "original":
+        raise ValueError("method must be 'original' or 'dipole'")
+    return out
+
+
+def doubled_fine_potential(rho_fine, geom, m, G=1.0, spectrum=None):
+    """Phi^m_dbl of Sect. 7 / Fig. 16: level m's mass on a grid of level-m cells
+    with twice as many cells per axis (2N), spanning level m-1.  The level-m
+    block sits in cells [N/2, 3N/2); the rest carries zero mass.  Returns the
+    potential on all (2N)^3 cells."""
+    N = geom.N
+    Mdbl = np.zeros((2 * N, 2 * N, 2 * N))
+    a, b = N // 2, 3 * N // 2
+    Mdbl[a:b, a:b, a:b] = rho_fine * geom.dx(m) ** 3
+    return isolated_convolution(Mdbl, geom.dx(m), G, spectrum)
+
+
+def solve(rho, N, dx0, G=1.0, method="original"):
+    """Potential on every cell of every level, shape (levels, N, N, N).
+
+    method='original' -- Eq. 14:
+        Phi(Omega^n) = Phi^n + sum_{k<n} tilde Phi^k_hole.
+    method='dipole'   -- pairwise dipole method, Eqs. 15 and B.1-B.2:
+        Phi(Omega^n) = Phi^n_hole + tilde Phi^{n+1}_dbl + sum_{k<n} tilde Phi^k_hole
+                       for n below the finest level,
+        Phi(Omega^L) = Phi^L + sum_{k<L} tilde Phi^k_hole on the finest.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    L = rho.shape[0]
+    comp = solve_components(rho, N, dx0, G, method)
+    out = np.zeros((L, N, N, N))
+    for n in range(L):
+        if method == "original" or n == L - 1:
+            phi = comp["full"][n].copy()
+        else:
+            phi = comp["hole"][n] + comp["dbl"][n]
+        for k in range(n):
+            phi += trilinear_to_level(comp["hole"][k], N, k, n)
+        out[n] = phi
+    return out

@@ -1,0 +1,73 @@
+"""Closed-form potentials used to pin the oracle (G = 1 unless given).
+
+Each is written from the mathematics (shell theorem, or the classical closed
+form for a uniform rectangular prism), independently of the oracle's code.
+"""
+import math
+
+import numpy as np
+
+
+def plummer(r, M, a, G=1.0):
+    return -G * M / np.sqrt(r * r + a * a)
+
+
+def uniform_sphere(r, M, R, G=1.0):
+    r = np.asarray(r, dtype=float)
+    inside = -G * M * (3.0 * R * R - r * r) / (2.0 * R ** 3)
+    with np.errstate(divide="ignore"):
+        outside = -G * M / np.where(r > 0, r, 1.0)
+    return np.where(r <= R, inside, outside)
+
+
+def poly_sphere(r, M, R, G=1.0):
+    """rho = rho0 (1 - s^2)^2, s = r/R, inside R.  Shell theorem:
+    Phi(r) = -G M(<r)/r - 4 pi G int_r^R rho(t) t dt."""
+    r = np.asarray(r, dtype=float)
+    rho0 = M / (4.0 * math.pi * R ** 3 * 8.0 / 105.0)
+    s = np.clip(r / R, 0.0, 1.0)
+    # M(<r) = 4 pi rho0 R^3 (s^3/3 - 2 s^5/5 + s^7/7)
+    m_in = 4.0 * math.pi * rho0 * R ** 3 * (s ** 3 / 3.0 - 2.0 * s ** 5 / 5.0 + s ** 7 / 7.0)
+    # int_r^R rho t dt = rho0 R^2 [F(1) - F(s)], F(s) = s^2/2 - s^4/2 + s^6/6
+    F = lambda u: u ** 2 / 2.0 - u ** 4 / 2.0 + u ** 6 / 6.0
+    outer = rho0 * R ** 2 * (F(1.0) - F(s))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        phi_in = np.where(r > 0, -G * m_in / np.where(r > 0, r, 1.0), 0.0) \
+            - 4.0 * math.pi * G * outer
+    phi_out = -G * M / np.where(r > 0, r, 1.0)
+    return np.where(r < R, phi_in, phi_out)
+
+
+def box_integral(px, py, pz, x1, x2, y1, y2, z1, z2):
+    """Integral of 1/|p - q| over q in the box [x1,x2]x[y1,y2]x[z1,z2].
+
+    Classical closed form: sum over the 8 corners with sign (-1)^(i+j+k) of
+      x y ln(z + R) + y z ln(x + R) + z x ln(y + R)
+      - x^2/2 atan(y z / (x R)) - y^2/2 atan(z x / (y R)) - z^2/2 atan(x y / (z R)),
+    (x, y, z) the corner relative to p and R its distance.  Terms whose
+    coefficient vanishes are dropped (their limits are zero).
+    """
+    def F(x, y, z):
+        R = math.sqrt(x * x + y * y + z * z)
+        v = 0.0
+        if x != 0 and y != 0:
+            v += x * y * math.log(z + R)
+        if y != 0 and z != 0:
+            v += y * z * math.log(x + R)
+        if z != 0 and x != 0:
+            v += z * x * math.log(y + R)
+        if x != 0:
+            v -= 0.5 * x * x * math.atan(y * z / (x * R))
+        if y != 0:
+            v -= 0.5 * y * y * math.atan(z * x / (y * R))
+        if z != 0:
+            v -= 0.5 * z * z * math.atan(x * y / (z * R))
+        return v
+
+    tot = 0.0
+    for i, X in enumerate((x1 - px, x2 - px)):
+        for j, Y in enumerate((y1 - py, y2 - py)):
+            for k, Z in enumerate((z1 - pz, z2 - pz)):
+                s = 1.0 if (i + j + k) % 2 == 1 else -1.0
+                tot += s * F(X, Y, Z)
+    return tot
