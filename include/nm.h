@@ -1,0 +1,160 @@
+/*
+ * nm.h -- C ABI of libnestconv: gravitational potential on nested Cartesian
+ * meshes by the convolution method (Vorobyov, McKevitt, Kulikov & Elbakyan
+ * 2023, "Computing the gravitational potential on nested meshes using the
+ * convolution method").
+ *
+ * What is computed
+ * ----------------
+ * A nested mesh has L levels m = 0 (coarsest) .. L-1 (finest), each of N^3
+ * cubic cells, all centred on the origin.  Level m has cell size
+ * dx_m = dx0 / 2^m (Sect. 2, Fig. 1: each level halves the physical size) and
+ * level m+1 covers level-m cells [N/4, 3N/4) on every axis.
+ *
+ * For each level the cell masses M = rho dx_m^3 are convolved with the inverse
+ * distance between cell centres, Phi_i = -G sum_j M_j calG(x_i - x_j)
+ * (Eq. 10), the self-cell term being the exact integral of 1/r over the cell,
+ * calG(0) = C / dx_m with C = 3 ln(2 + sqrt 3) - pi/2 (Eq. 13).  The sum is
+ * evaluated with the convolution theorem on the domain doubled to (2N)^3 and
+ * zero padded (Sect. 3, Eq. 11, Fig. 4), so it is the isolated sum exactly up
+ * to rounding.
+ *
+ * Levels are combined as in Sect. 4 (Fig. 5, Eq. 14):
+ *     Phi(Omega^n) = Phi^n + sum_{k<n} interp_{k->n}(Phi^k_hole)
+ * where Phi^k_hole is level k's potential with the covered cells' mass removed
+ * and interp is trilinear interpolation from level-k cell centres straight to
+ * level-n cell centres.  With NM_METHOD_DIPOLE_PAIR the pairwise dipole
+ * method of Sect. 7 and Appendix B (Eqs. 15, B.1-B.2) is used instead for
+ * every level but the finest:
+ *     Phi(Omega^n) = Phi^n_hole + reduce(Phi^{n+1}_dbl) + sum_{k<n} interp(Phi^k_hole)
+ * with Phi^{n+1}_dbl the potential of level n+1's mass on a (2N)^3 grid of
+ * level-(n+1) cells spanning level n, reduced to level n by the mean of the
+ * 2^3 fine values in each coarse cell.
+ *
+ * Covered coarse cells take the mean of their 2^3 finer children (swept from
+ * the finest level up), so the caller's values in those cells are ignored.
+ *
+ * Data layout
+ * -----------
+ * rho : L * N^3 densities, contiguous [level][z][y][x] (x fastest), level 0
+ *       coarsest.  double for NM_FP64 plans, float for NM_FP32 plans.
+ * phi : L * N^3 doubles, same layout; every cell of every level is written,
+ *       covered cells included.
+ * Pointers passed to nm_potential are DEVICE pointers (current device),
+ * owned by the caller; nm_potential_host takes HOST pointers.
+ *
+ * Streams and errors
+ * ------------------
+ * `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ * stream.  Calls that take a stream are asynchronous with respect to the host
+ * unless stated otherwise.  Argument errors are reported synchronously
+ * (NM_EINVAL / NM_EUNSUPPORTED) and nothing is launched.  A CUDA error seen
+ * at launch is returned as NM_ECUDA; errors of kernels still running surface
+ * at the caller's next synchronisation.  nm_last_error() returns a message for
+ * the calling thread's last failure.  Nothing here aborts the process.
+ *
+ * A plan owns its device workspace; calls that use the same plan must be
+ * ordered (same stream, or synchronised) because they share that workspace.
+ * Green spectra are cached per (device, N) and shared by all plans.
+ */
+#ifndef NESTCONV_NM_H
+#define NESTCONV_NM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nm_plan_s* nm_plan_t;
+
+typedef enum {
+    NM_OK = 0,
+    NM_EINVAL = 1,        /* bad argument (null pointer, bad size, bad option)   */
+    NM_ENOMEM = 2,        /* device or host allocation failed                   */
+    NM_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed        */
+    NM_ETIMEOUT = 4,      /* a bounded device-side wait gave up                 */
+    NM_EUNSUPPORTED = 5   /* valid request this build does not implement       */
+} nm_status;
+
+enum { NM_FP64 = 0, NM_FP32 = 1 };
+enum { NM_METHOD_ORIGINAL = 0, NM_METHOD_DIPOLE_PAIR = 1 };
+enum { NM_INTERP_TRILINEAR = 0 };
+enum { NM_MAX_LEVELS = 16 };
+
+typedef struct {
+    int levels;      /* L, 1 .. NM_MAX_LEVELS                                   */
+    int N;           /* cells per axis per level: a power of two, 4 .. 256      */
+    double dx0;      /* coarsest cell size (> 0); level m has dx0 / 2^m         */
+    double G;        /* gravitational constant (Eq. 9); nm_plan uses 1.0        */
+    int precision;   /* NM_FP64: all arithmetic in double.  NM_FP32: FFT passes,
+                        spectrum multiply and interpolation in float, Green
+                        spectrum built in double, final per-cell cross-level
+                        sum in double.                                          */
+    int method;      /* NM_METHOD_ORIGINAL (Eq. 14) or NM_METHOD_DIPOLE_PAIR
+                        (Eqs. 15, B.1-B.2)                                       */
+    int interp;      /* NM_INTERP_TRILINEAR (the only stencil built)            */
+} nm_options;
+
+/* Fill `opt` with the defaults used by nm_plan: G = 1, NM_FP64, original
+ * method, trilinear interpolation.  No device work. */
+nm_status nm_default_options(int levels, int N, double dx0, nm_options* opt);
+
+/* Create a plan for one nested mesh on the current CUDA device: validates the
+ * geometry (Sect. 2), allocates the plan's device workspace and the kernel
+ * schedule.  The Green spectrum is not built yet (see nm_green).
+ * `out` receives an opaque handle owned by the caller; free with nm_destroy.
+ * Errors: NM_EINVAL (bad sizes, null out), NM_EUNSUPPORTED (N outside the
+ * built range), NM_ENOMEM, NM_ECUDA. */
+nm_status nm_plan(int levels, int N, double dx0, nm_plan_t* out);
+nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out);
+
+/* Build (or take from the cache) the transform of the unit-cell kernel of
+ * Eq. 10 with the Eq. 13 self term on the doubled domain of Fig. 4, in double
+ * precision, on `stream`.  The spectrum is real and even, so only its octant
+ * (N+1)^3 is kept.  Idempotent; nm_potential calls it when needed. */
+nm_status nm_green(nm_plan_t plan, void* stream);
+
+/* The potential of every cell of every level (see the header comment) from
+ * densities `rho` (device, L*N^3, double or float by precision) into `phi`
+ * (device, L*N^3 double).  Asynchronous on `stream`.  `rho` is read only. */
+nm_status nm_potential(nm_plan_t plan, const void* rho, double* phi, void* stream);
+
+/* Same result from HOST buffers: copies rho to the device, solves, copies phi
+ * back, all on `stream`, and waits for the stream before returning.  Host
+ * buffers in pinned memory give asynchronous copies. */
+nm_status nm_potential_host(nm_plan_t plan, const void* rho_host, double* phi_host,
+                            void* stream);
+
+/* Device bytes held by the plan (workspace, excluding the shared spectrum),
+ * and the bytes of its share of the cached spectra; for admission control. */
+nm_status nm_workspace_bytes(nm_plan_t plan, size_t* bytes);
+nm_status nm_spectrum_bytes(nm_plan_t plan, size_t* bytes);
+
+/* Solve `n` independent meshes in one batched schedule on `stream`: the
+ * passes of all meshes and levels are grouped by kind into shared launches.
+ * plans[i], rho[i], phi[i] as for nm_potential; the plans must be distinct. */
+nm_status nm_batch_potential(int n, const nm_plan_t* plans, const void* const* rho,
+                             double* const* phi, void* stream);
+
+/* Copy the plan's unit-cell spectrum octant ((N+1)^3 doubles, [kz][ky][kx])
+ * to host memory `host_out`.  Synchronous.  Test hook. */
+nm_status nm_get_green_octant(nm_plan_t plan, double* host_out);
+
+/* Read the plan's options back. */
+nm_status nm_get_options(nm_plan_t plan, nm_options* out);
+
+/* Free the plan and its workspace (synchronises the device first). */
+nm_status nm_destroy(nm_plan_t plan);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t nm_kernel_launches(void);
+
+const char* nm_status_string(nm_status s);
+const char* nm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NESTCONV_NM_H */

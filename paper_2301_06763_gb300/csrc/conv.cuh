@@ -1,0 +1,250 @@
+// conv.cuh -- the per-level zero-padded convolution of Sect. 3 as five passes.
+//
+// Each launch transforms a set of "pairs": two real fields packed as one
+// complex field re + i*im.  The kernel spectrum is real (the inverse distance
+// of Eq. 10 is real and even on the doubled domain of Fig. 4), so the
+// convolution of the packed field is conv(re) + i*conv(im) and both come back
+// from one complex transform.
+//
+// Domain: FFT size P per axis.  Two geometries share the code:
+//   level grid (DBL = false): an N^3 block, N = P/2, sits at [0, N) (Fig. 4:
+//       the active region 1, regions 2-4 zero);
+//   doubled fine grid (DBL = true, Sect. 7 / Fig. 16): the fine level's N^3
+//       block sits at [N/2, 3N/2) of a 2N-cell grid, N = P/4, period P = 4N;
+//       any period >= 3N - 1 keeps the sum isolated.
+// In both the output window is [0, P/2) per axis.
+//
+// Work buffer of one pair: [Z = P/2][P][P] complex, index (z*P + y)*P + x.
+//   1 xfwd : rows (z, y) of the input block: mask, scale, pack, pad, FFT along x
+//   2 yfwd : slabs z of the input block, columns x: FFT along y (input pruned)
+//   3 zseam: lines (ky, kx): FFT along z, times the spectrum, inverse along z
+//   4 yinv : slabs z < P/2: inverse along y, keep y < P/2
+//   5 xinv : rows (z, y) < P/2: inverse along x, keep x < P/2, scatter outputs
+#pragma once
+#include "fft.cuh"
+
+namespace nm {
+
+enum SrcMode { SRC_NONE = 0, SRC_FULL = 1, SRC_HOLE = 2 };
+enum DstKind { DST_NONE = 0, DST_GRID = 1, DST_CROP = 2 };
+
+// One real input field: a level's density block (extent NL = N), the mean of
+// the finer level in its covered cells (restr, (NL/2)^3, may be null), the mode
+// (full grid, or hole grid with the covered cells emptied, Fig. 5) and the
+// factor turning density into the scaled mass the spectrum expects.
+struct SrcField {
+    const void* rho;
+    const void* restr;
+    int mode;
+    double scale;
+};
+struct DstField {
+    void* out;   // T*, extent P/2 grid or the hole crop
+    int kind;
+};
+template <typename T> struct PairDesc {
+    cpx<T>* work;
+    SrcField src[2];
+    DstField dst[2];
+};
+
+constexpr int kMaxPairs = 24;
+template <typename T> struct ConvArgs {
+    PairDesc<T> pair[kMaxPairs];
+    const T* spec;          // unit spectrum octant (P/2+1)^3, [kz][ky][kx]
+    const cpx<T>* tw;       // twiddle table, P entries
+};
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cpx<T>* sm_tw, const cpx<T>* tw, int P) {
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sm_tw[i] = tw[i];
+}
+
+// Density of a real field at block cell (z, y, x), already scaled.
+template <typename T, typename TIN>
+__device__ __forceinline__ T src_value(const SrcField& f, int NL, int z, int y, int x) {
+    if (f.mode == SRC_NONE) return T(0);
+    const int q = NL / 4, h = NL / 2;
+    const bool cov = (unsigned)(z - q) < (unsigned)h && (unsigned)(y - q) < (unsigned)h &&
+                     (unsigned)(x - q) < (unsigned)h;
+    double v;
+    if (cov) {
+        if (f.mode == SRC_HOLE) return T(0);
+        if (f.restr)
+            v = (double)((const TIN*)f.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)];
+        else
+            v = (double)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
+    } else {
+        v = (double)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
+    }
+    return T(v * f.scale);
+}
+
+template <int P, bool DBL> struct Geo {
+    static constexpr int NIN = DBL ? P / 4 : P / 2;   // input block extent
+    static constexpr int OFF = DBL ? P / 8 : 0;       // its offset in the domain
+    static constexpr int NOUT = P / 2;                // output window
+    // first-pass register r holds x[j + r P/8]: nonzero only for these r
+    __device__ static constexpr bool live(int r) { return DBL ? (r == 1 || r == 2) : (r < 4); }
+};
+
+// ---------------------------------------------------------------- pass 1
+template <typename T, typename TIN, int P, bool DBL>
+__global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T> a) {
+    using G = Geo<P, DBL>;
+    constexpr int TPL = P / 8;
+    constexpr int LINES = 256 / TPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* sm_lines = sm_tw + P;
+    const PairDesc<T>& d = a.pair[blockIdx.y];
+    load_twiddles(sm_tw, a.tw, P);
+    const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
+    const int row = blockIdx.x * LINES + line;
+    const bool valid = row < G::NIN * G::NIN;
+    const int zi = row / G::NIN, yi = row % G::NIN;
+    cpx<T> v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        v[r] = {T(0), T(0)};
+        if (G::live(r) && valid) {
+            const int xi = j + r * (P / 8) - G::OFF;
+            v[r].re = src_value<T, TIN>(d.src[0], G::NIN, zi, yi, xi);
+            v[r].im = src_value<T, TIN>(d.src[1], G::NIN, zi, yi, xi);
+        }
+    }
+    __syncthreads();
+    fft_line<T, P, false>(v, j, sm_tw, LineView<T, 1, true>{sm_lines + line * (P + P / 8)});
+    if (valid) {
+        cpx<T>* dst = d.work + ((size_t)(zi + G::OFF) * P + (yi + G::OFF)) * P;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) dst[out_index<P>(j, s)] = v[s];
+    }
+}
+
+// ---------------------------------------------------------------- passes 2, 4
+template <typename T, int P, int TX, bool INV, bool DBL>
+__global__ void __launch_bounds__(TX * P / 8) k_ypass(const __grid_constant__ ConvArgs<T> a) {
+    using G = Geo<P, DBL>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* sm_tile = sm_tw + P;
+    const PairDesc<T>& d = a.pair[blockIdx.z];
+    load_twiddles(sm_tw, a.tw, P);
+    const int l = threadIdx.x % TX, j = threadIdx.x / TX;
+    const int z = (INV ? 0 : G::OFF) + blockIdx.y;
+    const int x = blockIdx.x * TX + l;
+    cpx<T>* slab = d.work + (size_t)z * P * P;
+    cpx<T> v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (INV || G::live(r)) v[r] = slab[(size_t)(j + r * (P / 8)) * P + x];
+        else v[r] = {T(0), T(0)};
+    }
+    __syncthreads();
+    fft_line<T, P, INV>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int e = out_index<P>(j, s);
+        if (!INV || e < G::NOUT) slab[(size_t)e * P + x] = v[s];
+    }
+}
+
+// ---------------------------------------------------------------- pass 3
+template <typename T, int P, int TX, bool DBL>
+__global__ void __launch_bounds__(TX * P / 8) k_zseam(const __grid_constant__ ConvArgs<T> a) {
+    using G = Geo<P, DBL>;
+    constexpr int H = P / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* sm_tile = sm_tw + P;
+    const PairDesc<T>& d = a.pair[blockIdx.z];
+    load_twiddles(sm_tw, a.tw, P);
+    const int l = threadIdx.x % TX, j = threadIdx.x / TX;
+    const int y = blockIdx.y;
+    const int x = blockIdx.x * TX + l;
+    cpx<T>* col = d.work + (size_t)y * P + x;          // element z at col[z * P * P]
+    cpx<T> v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        if (G::live(r)) v[r] = col[(size_t)(j + r * (P / 8)) * P * P];
+        else v[r] = {T(0), T(0)};
+    }
+    __syncthreads();
+    const LineView<T, TX, false> view{sm_tile + l};
+    fft_line<T, P, false>(v, j, sm_tw, view);
+    const int fy = y <= P / 2 ? y : P - y;
+    const int fx = x <= P / 2 ? x : P - x;
+    const T* sp = a.spec + (size_t)fy * H + fx;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int kz = out_index<P>(j, s);
+        const int fz = kz <= P / 2 ? kz : P - kz;
+        const T g = __ldg(sp + (size_t)fz * H * H);
+        v[s].re *= g;
+        v[s].im *= g;
+    }
+    seam_permute<T, P>(v);
+    fft_line<T, P, true>(v, j, sm_tw, view);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int e = out_index<P>(j, s);
+        if (e < G::NOUT) col[(size_t)e * P * P] = v[s];
+    }
+}
+
+// ---------------------------------------------------------------- pass 5
+template <typename T, int P>
+__device__ __forceinline__ void store_out(const DstField& f, int z, int y, int x, T val) {
+    constexpr int E = P / 2;
+    if (f.kind == DST_GRID) {
+        ((T*)f.out)[((size_t)z * E + y) * E + x] = val;
+    } else if (f.kind == DST_CROP) {
+        const int c0 = E / 4 - 1, nc = E / 2 + 2;
+        if ((unsigned)(z - c0) < (unsigned)nc && (unsigned)(y - c0) < (unsigned)nc &&
+            (unsigned)(x - c0) < (unsigned)nc)
+            ((T*)f.out)[((size_t)(z - c0) * nc + (y - c0)) * nc + (x - c0)] = val;
+    }
+}
+
+template <typename T, int P, bool DBL>
+__global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T> a) {
+    constexpr int TPL = P / 8;
+    constexpr int LINES = 256 / TPL;
+    constexpr int E = P / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* sm_lines = sm_tw + P;
+    const PairDesc<T>& d = a.pair[blockIdx.y];
+    load_twiddles(sm_tw, a.tw, P);
+    const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
+    const int row = blockIdx.x * LINES + line;
+    const bool valid = row < E * E;
+    const int z = row / E, y = row % E;
+    cpx<T> v[8];
+    const cpx<T>* src = d.work + ((size_t)z * P + y) * P;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = valid ? src[j + r * (P / 8)] : cpx<T>{T(0), T(0)};
+    __syncthreads();
+    fft_line<T, P, true>(v, j, sm_tw, LineView<T, 1, true>{sm_lines + line * (P + P / 8)});
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int e = out_index<P>(j, s);
+            if (e < E) {
+                store_out<T, P>(d.dst[0], z, y, e, v[s].re);
+                store_out<T, P>(d.dst[1], z, y, e, v[s].im);
+            }
+        }
+    }
+}
+
+// Column tile width of the strided passes: 128-byte rows of the tile, at most
+// 1024 threads, never wider than a row of the domain.
+template <typename T, int P> struct Tile {
+    static constexpr int W = (sizeof(T) == 4 ? 16 : 8);
+    static constexpr int A = W < P ? W : P;
+    static constexpr int TX = (A * P / 8 > 1024) ? 8192 / P : A;
+};
+
+}  // namespace nm

@@ -1,0 +1,44 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "conv.cuh"
+
+namespace nm {
+
+// Counts every kernel launched by the library (reported by nm_kernel_launches).
+void count_launches(int n);
+
+// Five-pass convolution of `npairs` packed pairs of FFT size P (see conv.cuh).
+// DBL selects the doubled-fine-grid geometry.  Returns the first launch error.
+cudaError_t run_conv_f32(const PairDesc<float>* pairs, int npairs, int P, bool dbl,
+                         const float* spec, const cpx<float>* tw, cudaStream_t s);
+cudaError_t run_conv_f64(const PairDesc<double>* pairs, int npairs, int P, bool dbl,
+                         const double* spec, const cpx<double>* tw, cudaStream_t s);
+
+// Unit-cell kernel spectrum octant (N+1)^3 in double (Eqs. 10, 13, Fig. 4);
+// `scratch` holds 2 (N+1)^3 doubles, `ctab` the P = 2N cosines cos(2 pi t/P).
+cudaError_t run_green_octant(double* out, double* scratch, const double* ctab, int N,
+                             double self_term, cudaStream_t s);
+cudaError_t run_to_float(const double* in, float* out, size_t n, cudaStream_t s);
+
+// Restriction of level m+1 onto level m's covered cells (mean of 2^3 children).
+template <typename TIN>
+cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* restr_out, int N,
+                         cudaStream_t s);
+
+// Final assembly (Eq. 14 / Eqs. 15, B.1-B.2) into phi (double).
+template <typename T> struct AssembleArgs {
+    const T* base[16];     // per level: Phi^n (original) or Phi^n_hole (dipole), N^3
+    const T* dbl[16];      // per level: (2N)^3 doubled-grid potential to reduce, or null
+    const T* interp[16];   // per level k: source of the hole potential for finer levels
+    int interp_origin[16]; // level-k index of interp[k]'s first cell on each axis
+    int interp_extent[16]; // its extent per axis
+    double* phi;
+    int levels, N;
+};
+template <typename T>
+cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s);
+
+}  // namespace nm

@@ -1,0 +1,186 @@
+// support.cu -- restriction, Green spectrum and final assembly kernels.
+#include "internal.h"
+
+namespace nm {
+
+// ---------------------------------------------------------------- restriction
+// Covered cells of level m (index [N/4, 3N/4)^3) take the mean of their 2^3
+// children on level m+1 (Sect. 4 and Sect. 7: the coarse grid carries the fine
+// mass).  Children that are themselves covered by level m+2 take that level's
+// restricted value, so sweeping m from the finest level up gives every covered
+// cell the mean of the finest data below it.
+template <typename TIN>
+__global__ void k_restrict(const TIN* __restrict__ rho_child, const TIN* __restrict__ restr_child,
+                           TIN* __restrict__ out, int N) {
+    const int h = N / 2, q = N / 4;
+    const int n = h * h * h;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = i % h, b = (i / h) % h, a = i / (h * h);
+        double s = 0.0;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int z = 2 * a + dz, y = 2 * b + dy, x = 2 * c + dx;
+                    const bool cov = restr_child && (unsigned)(z - q) < (unsigned)h &&
+                                     (unsigned)(y - q) < (unsigned)h &&
+                                     (unsigned)(x - q) < (unsigned)h;
+                    s += cov ? (double)restr_child[((size_t)(z - q) * h + (y - q)) * h + (x - q)]
+                             : (double)rho_child[((size_t)z * N + y) * N + x];
+                }
+        out[i] = (TIN)(s * 0.125);
+    }
+}
+
+template <typename TIN>
+cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* restr_out, int N,
+                         cudaStream_t s) {
+    const int n = (N / 2) * (N / 2) * (N / 2);
+    const int blocks = (n + 255) / 256;
+    k_restrict<TIN><<<blocks, 256, 0, s>>>(rho_child, restr_child, restr_out, N);
+    count_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t run_restrict<float>(const float*, const float*, float*, int, cudaStream_t);
+template cudaError_t run_restrict<double>(const double*, const double*, double*, int, cudaStream_t);
+
+// ---------------------------------------------------------------- Green spectrum
+// The unit-cell kernel of Eq. 10 (1/|d| for integer offsets d != 0, the
+// Eq. 13 self term C at d = 0) on the doubled domain of Fig. 4 is real and even
+// in every axis, so its 3-D transform is real and even and equals a 3-D DCT-I
+// of the octant d in [0, N]^3:
+//   S(k) = sum_d w(dx) w(dy) w(dz) g(d) cos(2 pi kx dx/P) cos(..y..) cos(..z..),
+// w = 1 at d in {0, N}, 2 otherwise.  One axis per pass, all in double; the
+// cosines come from a table of cos(2 pi t / P) built on the host.
+__device__ __forceinline__ double green_unit(int a, int b, int c, double self_term) {
+    if ((a | b | c) == 0) return self_term;
+    return 1.0 / sqrt((double)a * a + (double)b * b + (double)c * c);
+}
+
+__global__ void k_green_fill(double* __restrict__ out, int N, double self_term) {
+    const int H = N + 1;
+    const size_t n = (size_t)H * H * H;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = green_unit((int)(i / ((size_t)H * H)), (int)((i / H) % H), (int)(i % H),
+                            self_term);
+}
+
+// one DCT-I pass along axis 0 (x, fastest), 1 (y) or 2 (z) of an H^3 array
+__global__ void k_green_axis(const double* __restrict__ in, double* __restrict__ out,
+                             const double* __restrict__ ctab, int N, int axis) {
+    const int H = N + 1, P = 2 * N;
+    const size_t n = (size_t)H * H * H;
+    const size_t stride = axis == 0 ? 1 : axis == 1 ? (size_t)H : (size_t)H * H;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)((i / stride) % H);
+        const size_t base = i - (size_t)k * stride;
+        double s = 0.0;
+        for (int d = 0; d <= N; ++d) {
+            const double w = (d == 0 || d == N) ? 1.0 : 2.0;
+            s += w * in[base + (size_t)d * stride] * ctab[(k * d) % P];
+        }
+        out[i] = s;
+    }
+}
+
+cudaError_t run_green_octant(double* out, double* scratch, const double* ctab, int N,
+                             double self_term, cudaStream_t s) {
+    const size_t H = N + 1;
+    const size_t n = H * H * H;
+    const int blocks = (int)((n + 255) / 256 < 152 * 64 ? (n + 255) / 256 : 152 * 64);
+    double* t1 = scratch;
+    double* t2 = scratch + n;
+    k_green_fill<<<blocks, 256, 0, s>>>(out, N, self_term);
+    k_green_axis<<<blocks, 256, 0, s>>>(out, t1, ctab, N, 0);
+    k_green_axis<<<blocks, 256, 0, s>>>(t1, t2, ctab, N, 1);
+    k_green_axis<<<blocks, 256, 0, s>>>(t2, out, ctab, N, 2);
+    count_launches(4);
+    return cudaGetLastError();
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+cudaError_t run_to_float(const double* in, float* out, size_t n, cudaStream_t s) {
+    const int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
+    k_to_float<<<blocks, 256, 0, s>>>(in, out, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- assembly
+// Phi(Omega^n) = base_n + reduce(dbl_n) + sum_{k<n} interp_{k->n}(hole_k).
+// Trilinear interpolation from level k straight to level n: the level-n
+// centre i sits at level-k fractional index
+//   u = N/2 - N/(2r) + (i + 1/2)/r - 1/2,  r = 2^(n-k),
+// i.e. 2r u = (N - 1)(r - 1) + 2i, so the stencil corner and weight follow in
+// integer arithmetic and the weights are exact.  Each interpolated term is
+// formed in T; the per-cell sum over levels is accumulated in double.
+template <typename T>
+__device__ __forceinline__ void axis_stencil(int N, int r, int i, int& i0, T& t) {
+    const int num = (N - 1) * (r - 1) + 2 * i;
+    i0 = num / (2 * r);
+    t = (T)(num - i0 * 2 * r) / (T)(2 * r);
+}
+
+template <typename T>
+__global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a) {
+    const int N = a.N;
+    const size_t N3 = (size_t)N * N * N;
+    const size_t total = N3 * a.levels;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int n = (int)(idx / N3);
+        const size_t cell = idx - (size_t)n * N3;
+        const int x = (int)(cell % N), y = (int)((cell / N) % N), z = (int)(cell / ((size_t)N * N));
+        double acc = (double)a.base[n][cell];
+        if (a.dbl[n]) {
+            const int E = 2 * N;
+            const T* d = a.dbl[n];
+            double s = 0.0;
+            for (int dz = 0; dz < 2; ++dz)
+                for (int dy = 0; dy < 2; ++dy) {
+                    const T* row = d + ((size_t)(2 * z + dz) * E + (2 * y + dy)) * E + 2 * x;
+                    s += (double)row[0] + (double)row[1];
+                }
+            acc += 0.125 * s;
+        }
+        for (int k = 0; k < n; ++k) {
+            const int r = 1 << (n - k);
+            int iz, iy, ix;
+            T tz, ty, tx;
+            axis_stencil<T>(N, r, z, iz, tz);
+            axis_stencil<T>(N, r, y, iy, ty);
+            axis_stencil<T>(N, r, x, ix, tx);
+            const int o = a.interp_origin[k], E = a.interp_extent[k];
+            const T* src = a.interp[k] + ((size_t)(iz - o) * E + (iy - o)) * E + (ix - o);
+            const size_t sz = (size_t)E * E, sy = E;
+            const T c00 = src[0] * (T(1) - tx) + src[1] * tx;
+            const T c01 = src[sy] * (T(1) - tx) + src[sy + 1] * tx;
+            const T c10 = src[sz] * (T(1) - tx) + src[sz + 1] * tx;
+            const T c11 = src[sz + sy] * (T(1) - tx) + src[sz + sy + 1] * tx;
+            const T c0 = c00 * (T(1) - ty) + c01 * ty;
+            const T c1 = c10 * (T(1) - ty) + c11 * ty;
+            acc += (double)(c0 * (T(1) - tz) + c1 * tz);
+        }
+        a.phi[idx] = acc;
+    }
+}
+
+template <typename T>
+cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
+    const size_t total = (size_t)a.N * a.N * a.N * a.levels;
+    size_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_assemble<T><<<(int)blocks, 256, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t run_assemble<float>(const AssembleArgs<float>&, cudaStream_t);
+template cudaError_t run_assemble<double>(const AssembleArgs<double>&, cudaStream_t);
+
+}  // namespace nm

@@ -1,0 +1,214 @@
+"""Python binding of libnestconv (the C ABI in include/nm.h).
+
+Argument marshalling only: every step of a solve runs in the CUDA library.  The
+library must have been built (``paper_2301_06763_gb300.build.build()``); when it
+is missing this module raises instead of computing anything another way.
+
+Tensors are PyTorch tensors (PyTorch provides device memory and streams):
+``rho`` is (levels, N, N, N) float64 (FP64 plans) or float32 (FP32 plans),
+contiguous, on the plan's device; ``phi`` is (levels, N, N, N) float64.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnestconv.so")
+
+NM_OK, NM_EINVAL, NM_ENOMEM, NM_ECUDA, NM_ETIMEOUT, NM_EUNSUPPORTED = range(6)
+FP64, FP32 = 0, 1
+ORIGINAL, DIPOLE_PAIR = 0, 1
+_PREC = {"fp64": FP64, "fp32": FP32}
+_METHOD = {"original": ORIGINAL, "dipole": DIPOLE_PAIR}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("N", ctypes.c_int), ("dx0", ctypes.c_double),
+                ("G", ctypes.c_double), ("precision", ctypes.c_int), ("method", ctypes.c_int),
+                ("interp", ctypes.c_int)]
+
+
+class NMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (status_string(status), message))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnestconv.so is not built (%s); run "
+                               "paper_2301_06763_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        st = ctypes.c_int
+        sig = {
+            "nm_default_options": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.POINTER(Options)]),
+            "nm_plan": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.POINTER(P)]),
+            "nm_plan_ex": (st, [ctypes.POINTER(Options), ctypes.POINTER(P)]),
+            "nm_green": (st, [P, P]),
+            "nm_potential": (st, [P, P, P, P]),
+            "nm_potential_host": (st, [P, P, P, P]),
+            "nm_workspace_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
+            "nm_spectrum_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
+            "nm_batch_potential": (st, [ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P),
+                                        ctypes.POINTER(P), P]),
+            "nm_get_green_octant": (st, [P, P]),
+            "nm_get_options": (st, [P, ctypes.POINTER(Options)]),
+            "nm_destroy": (st, [P]),
+            "nm_kernel_launches": (ctypes.c_uint64, []),
+            "nm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "nm_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().nm_status_string(int(s)).decode()
+
+
+def last_error():
+    return lib().nm_last_error().decode()
+
+
+def _check(status):
+    if status != NM_OK:
+        raise NMError(status, last_error())
+
+
+def kernel_launches():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().nm_kernel_launches())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """One nested mesh: ``levels`` levels of N^3 cells, coarsest cell ``dx0``."""
+
+    def __init__(self, levels, N, dx0, G=1.0, precision="fp64", method="original"):
+        o = Options()
+        _check(lib().nm_default_options(int(levels), int(N), float(dx0), ctypes.byref(o)))
+        o.G = float(G)
+        o.precision = _PREC[precision]
+        o.method = _METHOD[method]
+        h = ctypes.c_void_p()
+        _check(lib().nm_plan_ex(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.levels, self.N, self.dx0, self.G = int(levels), int(N), float(dx0), float(G)
+        self.precision, self.method = precision, method
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    @property
+    def shape(self):
+        return (self.levels, self.N, self.N, self.N)
+
+    @property
+    def rho_dtype(self):
+        import torch
+        return torch.float32 if self.precision == "fp32" else torch.float64
+
+    def green(self, stream=None):
+        _check(lib().nm_green(self.handle, _stream_handle(stream)))
+
+    def _check_tensor(self, t, dtype, name):
+        if t.dtype != dtype or tuple(t.shape) != self.shape or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("%s must be a contiguous CUDA %s tensor of shape %s" % (name, dtype, self.shape))
+
+    def potential(self, rho, phi=None, stream=None):
+        """Solve on the device; returns ``phi`` (allocated when not given)."""
+        import torch
+        self._check_tensor(rho, self.rho_dtype, "rho")
+        if phi is None:
+            phi = torch.empty(self.shape, dtype=torch.float64, device=rho.device)
+        self._check_tensor(phi, torch.float64, "phi")
+        _check(lib().nm_potential(self.handle, ctypes.c_void_p(rho.data_ptr()),
+                                  ctypes.c_void_p(phi.data_ptr()), _stream_handle(stream)))
+        return phi
+
+    def potential_host(self, rho, phi=None, stream=None):
+        """Solve from host memory (numpy arrays or CPU tensors); synchronous."""
+        rho_np = rho.numpy() if hasattr(rho, "numpy") and not isinstance(rho, np.ndarray) else rho
+        want = np.float32 if self.precision == "fp32" else np.float64
+        if rho_np.dtype != want or rho_np.shape != self.shape or not rho_np.flags.c_contiguous:
+            raise ValueError("rho must be a C-contiguous %s array of shape %s" % (want, self.shape))
+        if phi is None:
+            phi = np.empty(self.shape, dtype=np.float64)
+        phi_np = phi.numpy() if hasattr(phi, "numpy") and not isinstance(phi, np.ndarray) else phi
+        if phi_np.dtype != np.float64 or phi_np.shape != self.shape or not phi_np.flags.c_contiguous:
+            raise ValueError("phi must be a C-contiguous float64 array of shape %s" % (self.shape,))
+        _check(lib().nm_potential_host(self.handle, ctypes.c_void_p(rho_np.ctypes.data),
+                                       ctypes.c_void_p(phi_np.ctypes.data), _stream_handle(stream)))
+        return phi
+
+    def workspace_bytes(self):
+        v = ctypes.c_size_t()
+        _check(lib().nm_workspace_bytes(self.handle, ctypes.byref(v)))
+        return int(v.value)
+
+    def spectrum_bytes(self):
+        v = ctypes.c_size_t()
+        _check(lib().nm_spectrum_bytes(self.handle, ctypes.byref(v)))
+        return int(v.value)
+
+    def green_octant(self):
+        out = np.empty((self.N + 1,) * 3, dtype=np.float64)
+        _check(lib().nm_get_green_octant(self.handle, ctypes.c_void_p(out.ctypes.data)))
+        return out
+
+    def close(self):
+        if self._h is not None:
+            _check(lib().nm_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def batch_potential(plans, rhos, phis, stream=None):
+    """Solve several meshes in one batched schedule (see nm_batch_potential)."""
+    n = len(plans)
+    if not (len(rhos) == len(phis) == n):
+        raise ValueError("plans, rhos and phis must have the same length")
+    for p, r, f in zip(plans, rhos, phis):
+        p._check_tensor(r, p.rho_dtype, "rho")
+        import torch
+        p._check_tensor(f, torch.float64, "phi")
+    H = (ctypes.c_void_p * max(n, 1))(*[p.handle for p in plans])
+    R = (ctypes.c_void_p * max(n, 1))(*[r.data_ptr() for r in rhos])
+    F = (ctypes.c_void_p * max(n, 1))(*[f.data_ptr() for f in phis])
+    _check(lib().nm_batch_potential(n, H, R, F, _stream_handle(stream)))
+    return phis
