@@ -151,6 +151,22 @@ nm_status nm_destroy(nm_plan_t plan);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t nm_kernel_launches(void);
 
+/* Per-kernel timing for measurement.  While enabled, every kernel the library
+ * launches is bracketed by two CUDA events recorded on its own stream.
+ * nm_profile_enable(1) clears earlier records; nm_profile_read waits for the
+ * recorded events and writes up to `max` aggregated entries (one per kernel
+ * name: launches, units of work processed -- convolution pairs for the FFT
+ * passes, levels for the others -- and summed event time in ms) and their
+ * number to *count.  Host-side bookkeeping only; results are unchanged. */
+typedef struct {
+    char name[48];
+    uint64_t launches;
+    uint64_t units;
+    double total_ms;
+} nm_kernel_stat;
+nm_status nm_profile_enable(int on);
+nm_status nm_profile_read(nm_kernel_stat* out, int max, int* count);
+
 const char* nm_status_string(nm_status s);
 const char* nm_last_error(void);
 

@@ -20,6 +20,46 @@ void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order
 
 static thread_local std::string t_last_error;
 
+// ------------------------------------------------------------------ profiling
+struct ProfRecord {
+    std::string name;
+    int units;
+    cudaEvent_t a, b;
+};
+static std::atomic<bool> g_prof_on{false};
+static std::mutex g_prof_mu;
+static std::vector<ProfRecord> g_prof;
+
+ProfScope::ProfScope(const char* name, int units, cudaStream_t stream) : s(stream) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    ProfRecord r{name, units, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess) return;
+    if (cudaEventCreate(&r.b) != cudaSuccess) { cudaEventDestroy(r.a); return; }
+    cudaEventRecord(r.a, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    idx = (int)g_prof.size();
+    g_prof.push_back(r);
+}
+ProfScope::~ProfScope() {
+    if (idx < 0) return;
+    cudaEvent_t b;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (idx >= (int)g_prof.size()) return;
+        b = g_prof[idx].b;
+    }
+    cudaEventRecord(b, s);
+}
+
+static void prof_clear() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof.clear();
+}
+
 static nm_status fail(nm_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -532,6 +572,38 @@ nm_status nm_destroy(nm_plan_t p) {
 }
 
 uint64_t nm_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+nm_status nm_profile_enable(int on) {
+    if (on) prof_clear();
+    g_prof_on.store(on != 0);
+    return NM_OK;
+}
+
+nm_status nm_profile_read(nm_kernel_stat* out, int max, int* count) {
+    if (!count || (max > 0 && !out)) return fail(NM_EINVAL, "nm_profile_read: null argument");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::vector<nm_kernel_stat> agg;
+    for (auto& r : g_prof) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "profile events");
+        nm_kernel_stat* st = nullptr;
+        for (auto& a : agg)
+            if (r.name == a.name) { st = &a; break; }
+        if (!st) {
+            agg.push_back(nm_kernel_stat{});
+            st = &agg.back();
+            snprintf(st->name, sizeof st->name, "%s", r.name.c_str());
+        }
+        st->launches += 1;
+        st->units += (uint64_t)r.units;
+        st->total_ms += ms;
+    }
+    *count = (int)agg.size();
+    for (int i = 0; i < (int)agg.size() && i < max; ++i) out[i] = agg[i];
+    return NM_OK;
+}
 
 const char* nm_status_string(nm_status s) {
     switch (s) {

@@ -1,6 +1,8 @@
 // conv_inst.cuh -- host dispatch of the five convolution passes for one real
 // type; included once per precision (conv_f32.cu, conv_f64.cu).
 #pragma once
+#include <cstdio>
+
 #include "internal.h"
 
 namespace nm {
@@ -31,11 +33,34 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
     if (prepared != cudaSuccess) return prepared;
     const int rows_in = Gm::NIN * Gm::NIN;
     const int rows_out = Gm::NOUT * Gm::NOUT;
-    k_xfwd<T, T, P, DBL><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
-    k_ypass<T, P, TX, false, DBL><<<dim3(P / TX, Gm::NIN, np), TX * P / 8, sm_yz, s>>>(a);
-    k_zseam<T, P, TX, DBL><<<dim3(P / TX, P, np), TX * P / 8, sm_yz, s>>>(a);
-    k_ypass<T, P, TX, true, DBL><<<dim3(P / TX, Gm::NOUT, np), TX * P / 8, sm_yz, s>>>(a);
-    k_xinv<T, P, DBL><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+    char nm_[48];
+    const char* tag = sizeof(T) == 4 ? "f32" : "f64";
+    const char* geo = DBL ? "_dbl" : "";
+    {
+        snprintf(nm_, sizeof nm_, "xfwd%s_%s_P%d", geo, tag, P);
+        ProfScope ps(nm_, np, s);
+        k_xfwd<T, T, P, DBL><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+    }
+    {
+        snprintf(nm_, sizeof nm_, "yfwd%s_%s_P%d", geo, tag, P);
+        ProfScope ps(nm_, np, s);
+        k_ypass<T, P, TX, false, DBL><<<dim3(P / TX, Gm::NIN, np), TX * P / 8, sm_yz, s>>>(a);
+    }
+    {
+        snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
+        ProfScope ps(nm_, np, s);
+        k_zseam<T, P, TX, DBL><<<dim3(P / TX, P, np), TX * P / 8, sm_yz, s>>>(a);
+    }
+    {
+        snprintf(nm_, sizeof nm_, "yinv%s_%s_P%d", geo, tag, P);
+        ProfScope ps(nm_, np, s);
+        k_ypass<T, P, TX, true, DBL><<<dim3(P / TX, Gm::NOUT, np), TX * P / 8, sm_yz, s>>>(a);
+    }
+    {
+        snprintf(nm_, sizeof nm_, "xinv%s_%s_P%d", geo, tag, P);
+        ProfScope ps(nm_, np, s);
+        k_xinv<T, P, DBL><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+    }
     count_launches(5);
     return cudaGetLastError();
 }

@@ -10,6 +10,16 @@ namespace nm {
 // Counts every kernel launched by the library (reported by nm_kernel_launches).
 void count_launches(int n);
 
+// Event bracket around one launch while profiling is on (nm_profile_enable).
+struct ProfScope {
+    int idx = -1;
+    cudaStream_t s = nullptr;
+    ProfScope(const char* name, int units, cudaStream_t stream);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+};
+
 // Five-pass convolution of `npairs` packed pairs of FFT size P (see conv.cuh).
 // DBL selects the doubled-fine-grid geometry.  Returns the first launch error.
 cudaError_t run_conv_f32(const PairDesc<float>* pairs, int npairs, int P, bool dbl,

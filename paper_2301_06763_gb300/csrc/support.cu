@@ -36,6 +36,7 @@ cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* rest
                          cudaStream_t s) {
     const int n = (N / 2) * (N / 2) * (N / 2);
     const int blocks = (n + 255) / 256;
+    ProfScope ps(sizeof(TIN) == 4 ? "restrict_f32" : "restrict_f64", 1, s);
     k_restrict<TIN><<<blocks, 256, 0, s>>>(rho_child, restr_child, restr_out, N);
     count_launches(1);
     return cudaGetLastError();
@@ -91,6 +92,7 @@ cudaError_t run_green_octant(double* out, double* scratch, const double* ctab, i
     const int blocks = (int)((n + 255) / 256 < 152 * 64 ? (n + 255) / 256 : 152 * 64);
     double* t1 = scratch;
     double* t2 = scratch + n;
+    ProfScope ps("green_octant", 1, s);
     k_green_fill<<<blocks, 256, 0, s>>>(out, N, self_term);
     k_green_axis<<<blocks, 256, 0, s>>>(out, t1, ctab, N, 0);
     k_green_axis<<<blocks, 256, 0, s>>>(t1, t2, ctab, N, 1);
@@ -176,6 +178,7 @@ cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
     const size_t total = (size_t)a.N * a.N * a.N * a.levels;
     size_t blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
+    ProfScope ps(sizeof(T) == 4 ? "assemble_f32" : "assemble_f64", a.levels, s);
     k_assemble<T><<<(int)blocks, 256, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();

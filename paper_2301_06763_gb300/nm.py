@@ -29,6 +29,11 @@ class Options(ctypes.Structure):
                 ("interp", ctypes.c_int)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64),
+                ("units", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
 class NMError(RuntimeError):
     def __init__(self, status, message):
         super().__init__("%s: %s" % (status_string(status), message))
@@ -64,6 +69,9 @@ def lib():
             "nm_get_options": (st, [P, ctypes.POINTER(Options)]),
             "nm_destroy": (st, [P]),
             "nm_kernel_launches": (ctypes.c_uint64, []),
+            "nm_profile_enable": (st, [ctypes.c_int]),
+            "nm_profile_read": (st, [ctypes.POINTER(KernelStat), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int)]),
             "nm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "nm_last_error": (ctypes.c_char_p, []),
         }
@@ -91,6 +99,21 @@ def _check(status):
 def kernel_launches():
     """Kernels launched by the library so far in this process."""
     return int(lib().nm_kernel_launches())
+
+
+def profile_enable(on=True):
+    """Bracket every library kernel with CUDA events (see nm_profile_enable)."""
+    _check(lib().nm_profile_enable(1 if on else 0))
+
+
+def profile_read():
+    """{kernel name: (launches, units, total_ms)} since profile_enable(True)."""
+    cap = 256
+    arr = (KernelStat * cap)()
+    n = ctypes.c_int()
+    _check(lib().nm_profile_read(arr, cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), int(arr[i].units), float(arr[i].total_ms))
+            for i in range(min(n.value, cap))}
 
 
 def _stream_handle(stream):
