@@ -167,6 +167,27 @@ typedef struct {
 nm_status nm_profile_enable(int on);
 nm_status nm_profile_read(nm_kernel_stat* out, int max, int* count);
 
+/* Allocation-free solve.  No counterpart in the paper: this entry point exists
+ * for callers that cannot call cudaMalloc while they run -- codes that size
+ * their device pools at start-up and forbid later allocations, processes whose
+ * device memory belongs to another framework's allocator, and loops that
+ * cannot afford cudaMalloc's implicit device-wide synchronisation.
+ * It computes the same potential as nm_potential (original method, Eq. 14) for
+ * the mesh described by `opt` (method must be NM_METHOD_ORIGINAL), from device
+ * `rho` to device `phi`, asynchronously on `stream`, and never allocates: all
+ * scratch (spectrum, tables, work buffer, level potentials) lives in one
+ * file-scope device array of NM_NOALLOC_SCRATCH_BYTES that every GPU loading
+ * the library holds until exit.  Meshes whose scratch would not fit are
+ * rejected with NM_EINVAL and a message giving the bytes needed (N <= 32 fits
+ * for every level count in FP32 and up to 15 levels in FP64; N = 64 does not).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (each call writes every region before reading it); calls that
+ * overlap on the GPU race on it, so serialise them. */
+#define NM_NOALLOC_SCRATCH_BYTES (8u << 20)
+nm_status nm_potential_noalloc(const nm_options* opt, const void* rho, double* phi, void* stream);
+
 const char* nm_status_string(nm_status s);
 const char* nm_last_error(void);
 

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnestconv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["conv_f32.cu", "conv_f64.cu", "support.cu", "api.cu"]
+UNITS = ["conv_f32.cu", "conv_f64.cu", "support.cu", "api.cu", "noalloc.cu"]
 
 
 def nvcc():

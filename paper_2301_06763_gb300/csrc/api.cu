@@ -70,6 +70,9 @@ static nm_status fail(nm_status st, const char* fmt, ...) {
     return st;
 }
 
+// Sets the calling thread's nm_last_error message from another translation unit.
+nm_status record_error(nm_status st, const char* msg) { return fail(st, "%s", msg); }
+
 static nm_status cuda_fail(cudaError_t e, const char* what) {
     return fail(e == cudaErrorMemoryAllocation ? NM_ENOMEM : NM_ECUDA, "%s: %s (%s)", what,
                 cudaGetErrorName(e), cudaGetErrorString(e));
