@@ -60,39 +60,44 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* sm_tw, const cpx<T>* tw, i
     for (int i = threadIdx.x; i < P; i += blockDim.x) sm_tw[i] = tw[i];
 }
 
-// Density of a real field at block cell (z, y, x), already scaled.
+// Density of a real field at block cell (z, y, x), already scaled.  All in
+// the pass precision T.
 template <typename T, typename TIN>
-__device__ __forceinline__ T src_value(const SrcField& f, int NL, int z, int y, int x) {
+__device__ __forceinline__ T src_value(const SrcField& f, T scale, int NL, int z, int y, int x) {
     if (f.mode == SRC_NONE) return T(0);
     const int q = NL / 4, h = NL / 2;
     const bool cov = (unsigned)(z - q) < (unsigned)h && (unsigned)(y - q) < (unsigned)h &&
                      (unsigned)(x - q) < (unsigned)h;
-    double v;
+    T v;
     if (cov) {
         if (f.mode == SRC_HOLE) return T(0);
         if (f.restr)
-            v = (double)((const TIN*)f.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)];
+            v = (T)((const TIN*)f.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)];
         else
-            v = (double)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
+            v = (T)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
     } else {
-        v = (double)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
+        v = (T)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
     }
-    return T(v * f.scale);
+    return v * scale;
 }
 
 template <int P, bool DBL> struct Geo {
+    static constexpr int E = EOf<P>::value;
     static constexpr int NIN = DBL ? P / 4 : P / 2;   // input block extent
     static constexpr int OFF = DBL ? P / 8 : 0;       // its offset in the domain
     static constexpr int NOUT = P / 2;                // output window
-    // first-pass register r holds x[j + r P/8]: nonzero only for these r
-    __device__ static constexpr bool live(int r) { return DBL ? (r == 1 || r == 2) : (r < 4); }
+    // first-pass register r holds x[j + r P/E]: nonzero only for these r
+    __device__ static constexpr bool live(int r) {
+        return DBL ? (r >= E / 8 && r < 3 * E / 8) : (r < E / 2);
+    }
 };
 
 // ---------------------------------------------------------------- pass 1
 template <typename T, typename TIN, int P, bool DBL>
 __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T> a) {
     using G = Geo<P, DBL>;
-    constexpr int TPL = P / 8;
+    constexpr int E = EOf<P>::value;
+    constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -103,29 +108,32 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
     const int row = blockIdx.x * LINES + line;
     const bool valid = row < G::NIN * G::NIN;
     const int zi = row / G::NIN, yi = row % G::NIN;
-    cpx<T> v[8];
+    const T s0 = (T)d.src[0].scale, s1 = (T)d.src[1].scale;
+    cpx<T> v[E];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < E; ++r) {
         v[r] = {T(0), T(0)};
         if (G::live(r) && valid) {
-            const int xi = j + r * (P / 8) - G::OFF;
-            v[r].re = src_value<T, TIN>(d.src[0], G::NIN, zi, yi, xi);
-            v[r].im = src_value<T, TIN>(d.src[1], G::NIN, zi, yi, xi);
+            const int xi = j + r * (P / E) - G::OFF;
+            v[r].re = src_value<T, TIN>(d.src[0], s0, G::NIN, zi, yi, xi);
+            v[r].im = src_value<T, TIN>(d.src[1], s1, G::NIN, zi, yi, xi);
         }
     }
     __syncthreads();
-    fft_line<T, P, false>(v, j, sm_tw, LineView<T, 1, true>{sm_lines + line * (P + P / 8)});
+    fft_line<T, P, false>(v, j, sm_tw,
+                          LineView<T, 1, true, EOf<P>::log2>{sm_lines + line * (P + P / E)});
     if (valid) {
         cpx<T>* dst = d.work + ((size_t)(zi + G::OFF) * P + (yi + G::OFF)) * P;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) dst[out_index<P>(j, s)] = v[s];
+        for (int s = 0; s < E; ++s) dst[out_index<P>(j, s)] = v[s];
     }
 }
 
 // ---------------------------------------------------------------- passes 2, 4
 template <typename T, int P, int TX, bool INV, bool DBL>
-__global__ void __launch_bounds__(TX * P / 8) k_ypass(const __grid_constant__ ConvArgs<T> a) {
+__global__ void __launch_bounds__(TX * P / EOf<P>::value) k_ypass(const __grid_constant__ ConvArgs<T> a) {
     using G = Geo<P, DBL>;
+    constexpr int E = EOf<P>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
@@ -135,16 +143,16 @@ __global__ void __launch_bounds__(TX * P / 8) k_ypass(const __grid_constant__ Co
     const int z = (INV ? 0 : G::OFF) + blockIdx.y;
     const int x = blockIdx.x * TX + l;
     cpx<T>* slab = d.work + (size_t)z * P * P;
-    cpx<T> v[8];
+    cpx<T> v[E];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        if (INV || G::live(r)) v[r] = slab[(size_t)(j + r * (P / 8)) * P + x];
+    for (int r = 0; r < E; ++r) {
+        if (INV || G::live(r)) v[r] = slab[(size_t)(j + r * (P / E)) * P + x];
         else v[r] = {T(0), T(0)};
     }
     __syncthreads();
     fft_line<T, P, INV>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < E; ++s) {
         const int e = out_index<P>(j, s);
         if (!INV || e < G::NOUT) slab[(size_t)e * P + x] = v[s];
     }
@@ -152,8 +160,9 @@ __global__ void __launch_bounds__(TX * P / 8) k_ypass(const __grid_constant__ Co
 
 // ---------------------------------------------------------------- pass 3
 template <typename T, int P, int TX, bool DBL>
-__global__ void __launch_bounds__(TX * P / 8) k_zseam(const __grid_constant__ ConvArgs<T> a) {
+__global__ void __launch_bounds__(TX * P / EOf<P>::value) k_zseam(const __grid_constant__ ConvArgs<T> a) {
     using G = Geo<P, DBL>;
+    constexpr int E = EOf<P>::value;
     constexpr int H = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -164,10 +173,10 @@ __global__ void __launch_bounds__(TX * P / 8) k_zseam(const __grid_constant__ Co
     const int y = blockIdx.y;
     const int x = blockIdx.x * TX + l;
     cpx<T>* col = d.work + (size_t)y * P + x;          // element z at col[z * P * P]
-    cpx<T> v[8];
+    cpx<T> v[E];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        if (G::live(r)) v[r] = col[(size_t)(j + r * (P / 8)) * P * P];
+    for (int r = 0; r < E; ++r) {
+        if (G::live(r)) v[r] = col[(size_t)(j + r * (P / E)) * P * P];
         else v[r] = {T(0), T(0)};
     }
     __syncthreads();
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(TX * P / 8) k_zseam(const __grid_constant__ Co
     const int fx = x <= P / 2 ? x : P - x;
     const T* sp = a.spec + (size_t)fy * H + fx;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < E; ++s) {
         const int kz = out_index<P>(j, s);
         const int fz = kz <= P / 2 ? kz : P - kz;
         const T g = __ldg(sp + (size_t)fz * H * H);
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(TX * P / 8) k_zseam(const __grid_constant__ Co
     seam_permute<T, P>(v);
     fft_line<T, P, true>(v, j, sm_tw, view);
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < E; ++s) {
         const int e = out_index<P>(j, s);
         if (e < G::NOUT) col[(size_t)e * P * P] = v[s];
     }
@@ -209,9 +218,10 @@ __device__ __forceinline__ void store_out(const DstField& f, int z, int y, int x
 
 template <typename T, int P, bool DBL>
 __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T> a) {
-    constexpr int TPL = P / 8;
+    constexpr int E = EOf<P>::value;
+    constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
-    constexpr int E = P / 2;
+    constexpr int HALF = P / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
@@ -219,19 +229,20 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
     load_twiddles(sm_tw, a.tw, P);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int row = blockIdx.x * LINES + line;
-    const bool valid = row < E * E;
-    const int z = row / E, y = row % E;
-    cpx<T> v[8];
+    const bool valid = row < HALF * HALF;
+    const int z = row / HALF, y = row % HALF;
+    cpx<T> v[E];
     const cpx<T>* src = d.work + ((size_t)z * P + y) * P;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = valid ? src[j + r * (P / 8)] : cpx<T>{T(0), T(0)};
+    for (int r = 0; r < E; ++r) v[r] = valid ? src[j + r * (P / E)] : cpx<T>{T(0), T(0)};
     __syncthreads();
-    fft_line<T, P, true>(v, j, sm_tw, LineView<T, 1, true>{sm_lines + line * (P + P / 8)});
+    fft_line<T, P, true>(v, j, sm_tw,
+                         LineView<T, 1, true, EOf<P>::log2>{sm_lines + line * (P + P / E)});
     if (valid) {
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
+        for (int s = 0; s < E; ++s) {
             const int e = out_index<P>(j, s);
-            if (e < E) {
+            if (e < HALF) {
                 store_out<T, P>(d.dst[0], z, y, e, v[s].re);
                 store_out<T, P>(d.dst[1], z, y, e, v[s].im);
             }
@@ -242,9 +253,10 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
 // Column tile width of the strided passes: 128-byte rows of the tile, at most
 // 1024 threads, never wider than a row of the domain.
 template <typename T, int P> struct Tile {
+    static constexpr int E = EOf<P>::value;
     static constexpr int W = (sizeof(T) == 4 ? 16 : 8);
     static constexpr int A = W < P ? W : P;
-    static constexpr int TX = (A * P / 8 > 1024) ? 8192 / P : A;
+    static constexpr int TX = (A * P / E > 1024) ? 1024 * E / P : A;
 };
 
 }  // namespace nm

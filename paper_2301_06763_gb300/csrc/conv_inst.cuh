@@ -15,11 +15,13 @@ static cudaError_t prep_kernel(K kernel, size_t smem) {
 template <typename T, int P, bool DBL>
 static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
     using Gm = Geo<P, DBL>;
-    constexpr int TPL = P / 8;
+    constexpr int E = EOf<P>::value;
+    constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     constexpr int TX = Tile<T, P>::TX;
+    constexpr int NT = TX * P / E;   // threads of the strided passes
     const size_t c = sizeof(cpx<T>);
-    const size_t sm_x = (size_t)P * c + (size_t)LINES * (P + P / 8) * c;
+    const size_t sm_x = (size_t)P * c + (size_t)LINES * (P + P / E) * c;
     const size_t sm_yz = (size_t)P * c + (size_t)TX * P * c;
     // shared-memory limits are set once per kernel (thread-safe static init)
     static const cudaError_t prepared = [&]() {
@@ -44,17 +46,17 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
     {
         snprintf(nm_, sizeof nm_, "yfwd%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_ypass<T, P, TX, false, DBL><<<dim3(P / TX, Gm::NIN, np), TX * P / 8, sm_yz, s>>>(a);
+        k_ypass<T, P, TX, false, DBL><<<dim3(P / TX, Gm::NIN, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_zseam<T, P, TX, DBL><<<dim3(P / TX, P, np), TX * P / 8, sm_yz, s>>>(a);
+        k_zseam<T, P, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "yinv%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_ypass<T, P, TX, true, DBL><<<dim3(P / TX, Gm::NOUT, np), TX * P / 8, sm_yz, s>>>(a);
+        k_ypass<T, P, TX, true, DBL><<<dim3(P / TX, Gm::NOUT, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "xinv%s_%s_P%d", geo, tag, P);

@@ -1,16 +1,17 @@
 // fft.cuh -- in-CTA Stockham FFT of one line of length P (power of two, 8..1024).
 //
 // The convolution theorem (Sect. 3, Eq. 11) is applied with discrete Fourier
-// transforms on the doubled domain.  Each line is transformed by P/8 threads,
-// each holding 8 complex values in registers.  The first pass is radix 8 on
-// the values the thread loaded itself (no twiddles); the remaining passes are
-// radix 8 while the remaining factor allows, then one radix-4 or radix-2 pass,
-// exchanging through shared memory between passes (self-sorting Stockham
-// order, so no bit reversal).
+// transforms on the doubled domain.  Each line is transformed by P/E threads,
+// each holding E complex values in registers (E = 16 for P >= 16, else 8).
+// The first pass is radix E on the values the thread loaded itself (no
+// twiddles); the remaining passes are radix E while the remaining factor
+// allows, then one radix-2/4/8 pass, exchanging through shared memory between
+// passes (self-sorting Stockham order, so no bit reversal).  P = 32..256 thus
+// needs one shared-memory round trip per transform.
 //
-// Register conventions (j = the thread's index within its line, 0 <= j < P/8):
-//   input : v[r] = x[j + r * P/8],                         r = 0..7
-//   output: v[b * R + r] = X[(j + b * P/8) + r * (P/R)],   b < 8/R, r < R
+// Register conventions (j = the thread's index within its line, 0 <= j < P/E):
+//   input : v[r] = x[j + r * P/E],                         r = 0..E-1
+//   output: v[b * R + r] = X[(j + b * P/E) + r * (P/R)],   b < E/R, r < R
 // where R is the radix of the last pass.  `seam_permute` maps an output
 // distribution onto the input distribution of a second transform held by the
 // same thread, so a forward transform, a pointwise multiply and an inverse
@@ -87,28 +88,82 @@ template <typename T, bool INV> __device__ __forceinline__ void dft8(cpx<T>* v) 
     v[1] = w[0]; v[3] = w[1]; v[5] = w[2]; v[7] = w[3];
 }
 
+// multiply by cos(a) -+ i sin(a) (forward / inverse)
+template <typename T, bool INV> __device__ __forceinline__ cpx<T> rotc(cpx<T> a, T c, T s) {
+    if (INV) return {a.re * c - a.im * s, a.re * s + a.im * c};
+    return {a.re * c + a.im * s, a.im * c - a.re * s};
+}
+
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.  DFT4 over n1 for each
+// n2, multiply by W16^(n2 k1), DFT4 over n2 for each k1.
+template <typename T, bool INV> __device__ __forceinline__ void dft16(cpx<T>* v) {
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+    cpx<T> y[16];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        cpx<T> t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+        dft4<T, INV>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) y[n2 * 4 + k1] = t[k1];
+    }
+    y[5] = rotc<T, INV>(y[5], c1, s1);      // W16^1
+    y[6] = rot8<T, INV>(y[6]);              // W16^2
+    y[7] = rotc<T, INV>(y[7], s1, c1);      // W16^3
+    y[9] = rot8<T, INV>(y[9]);              // W16^2
+    y[10] = rot4<T, INV>(y[10]);            // W16^4
+    y[11] = rot8_3<T, INV>(y[11]);          // W16^6
+    y[13] = rotc<T, INV>(y[13], s1, c1);    // W16^3
+    y[14] = rot8_3<T, INV>(y[14]);          // W16^6
+    y[15] = rotc<T, INV>(y[15], -c1, -s1);  // W16^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        cpx<T> t[4] = {y[k1], y[4 + k1], y[8 + k1], y[12 + k1]};
+        dft4<T, INV>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
 template <typename T, bool INV, int R> __device__ __forceinline__ void dftR(cpx<T>* v) {
-    if (R == 8) dft8<T, INV>(v);
-    else if (R == 4) dft4<T, INV>(v);
+    if constexpr (R == 16) dft16<T, INV>(v);
+    else if constexpr (R == 8) dft8<T, INV>(v);
+    else if constexpr (R == 4) dft4<T, INV>(v);
     else dft2<T, INV>(v);
 }
 
+// Values per thread for a line of length P.
+template <int P> struct EOf {
+    static constexpr int value = P >= 16 ? 16 : 8;
+    static constexpr int log2 = P >= 16 ? 4 : 3;
+};
+
 // Radix of the pass that starts at stride NS, and of the last pass.
 template <int P, int NS> struct PassRadix {
+    static constexpr int E = EOf<P>::value;
     static constexpr int REM = P / NS;
-    static constexpr int R = REM >= 8 ? 8 : REM;
+    static constexpr int R = REM >= E ? E : REM;
 };
 template <int P> struct LastRadix {
-    static constexpr int value = (P == 8 || P == 64 || P == 512) ? 8
-                               : (P == 32 || P == 256) ? 4 : 2;
+    static constexpr int calc() {
+        const int E = EOf<P>::value;
+        int ns = E, R = E;
+        while (ns < P) {
+            R = (P / ns >= E) ? E : P / ns;
+            ns *= R;
+        }
+        return R;
+    }
+    static constexpr int value = calc();
 };
 
 // Shared-memory view of the lines a CTA transforms.  Element e of the
-// calling thread's line lives at base[e * ES] (+ padding for contiguous lines).
-template <typename T, int ES, bool PAD> struct LineView {
+// calling thread's line lives at base[e * ES] (+ one padding slot every E
+// elements for contiguous lines, which keeps the first-pass stores of a warp
+// free of bank conflicts).
+template <typename T, int ES, bool PAD, int LOGE = 4> struct LineView {
     cpx<T>* base;
     __device__ __forceinline__ int off(int e) const {
-        return PAD ? (e + (e >> 3)) * ES : e * ES;
+        return PAD ? (e + (e >> LOGE)) * ES : e * ES;
     }
     __device__ __forceinline__ cpx<T> ld(int e) const { return base[off(e)]; }
     __device__ __forceinline__ void st(int e, cpx<T> v) const { base[off(e)] = v; }
@@ -124,19 +179,20 @@ __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* tw, int t) {
 // Passes after the first.  NS = product of the radices done so far.
 template <typename T, int P, bool INV, int NS, class View>
 __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
+    constexpr int E = EOf<P>::value;
     constexpr int R = PassRadix<P, NS>::R;
-    constexpr int NB = 8 / R;
+    constexpr int NB = E / R;
     constexpr bool LAST = (NS * R == P);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int jj = j + b * (P / 8);
+        const int jj = j + b * (P / E);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b * R + r] = sm.ld(jj + r * (P / R));
     }
     __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int jj = j + b * (P / 8);
+        const int jj = j + b * (P / E);
         const int k = jj & (NS - 1);
 #pragma unroll
         for (int r = 1; r < R; ++r)
@@ -146,7 +202,7 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
     if constexpr (!LAST) {
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            const int jj = j + b * (P / 8);
+            const int jj = j + b * (P / E);
             const int k = jj & (NS - 1);
             const int base = (jj / NS) * NS * R + k;
 #pragma unroll
@@ -161,29 +217,32 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
 // __syncthreads); the shared-memory line must not be in use by anyone else.
 template <typename T, int P, bool INV, class View>
 __device__ __forceinline__ void fft_line(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
-    dft8<T, INV>(v);
-    if constexpr (P > 8) {
+    constexpr int E = EOf<P>::value;
+    dftR<T, INV, E>(v);
+    if constexpr (P > E) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) sm.st(8 * j + r, v[r]);
+        for (int r = 0; r < E; ++r) sm.st(E * j + r, v[r]);
         __syncthreads();
-        fft_rest<T, P, INV, 8>(v, j, tw, sm);
+        fft_rest<T, P, INV, E>(v, j, tw, sm);
     }
 }
 
 // Output index of register slot s after fft_line (see the header comment).
 template <int P> __device__ __forceinline__ int out_index(int j, int s) {
+    constexpr int E = EOf<P>::value;
     constexpr int R = LastRadix<P>::value;
-    return j + (s / R) * (P / 8) + (s % R) * (P / R);
+    return j + (s / R) * (P / E) + (s % R) * (P / R);
 }
 
 // Output distribution -> input distribution, same thread:
-// in[b + r * (8/R)] = out[b * R + r].
+// in[b + r * (E/R)] = out[b * R + r].
 template <typename T, int P> __device__ __forceinline__ void seam_permute(cpx<T>* v) {
+    constexpr int E = EOf<P>::value;
     constexpr int R = LastRadix<P>::value;
-    constexpr int NB = 8 / R;
-    cpx<T> t[8];
+    constexpr int NB = E / R;
+    cpx<T> t[E];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) t[s] = v[s];
+    for (int s = 0; s < E; ++s) t[s] = v[s];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll

@@ -3,6 +3,12 @@
 
 namespace nm {
 
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
 // ---------------------------------------------------------------- restriction
 // Covered cells of level m (index [N/4, 3N/4)^3) take the mean of their 2^3
 // children on level m+1 (Sect. 4 and Sect. 7: the coarse grid carries the fine
@@ -11,23 +17,26 @@ namespace nm {
 // cell the mean of the finest data below it.
 template <typename TIN>
 __global__ void k_restrict(const TIN* __restrict__ rho_child, const TIN* __restrict__ restr_child,
-                           TIN* __restrict__ out, int N) {
-    const int h = N / 2, q = N / 4;
+                           TIN* __restrict__ out, int lgN) {
+    const int N = 1 << lgN, h = N / 2, q = N / 4, lgh = lgN - 1;
     const int n = h * h * h;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = i % h, b = (i / h) % h, a = i / (h * h);
-        double s = 0.0;
+        const int c = i & (h - 1), b = (i >> lgh) & (h - 1), a = i >> (2 * lgh);
+        TIN s = TIN(0);
+#pragma unroll
         for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
             for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
                     const int z = 2 * a + dz, y = 2 * b + dy, x = 2 * c + dx;
                     const bool cov = restr_child && (unsigned)(z - q) < (unsigned)h &&
                                      (unsigned)(y - q) < (unsigned)h &&
                                      (unsigned)(x - q) < (unsigned)h;
-                    s += cov ? (double)restr_child[((size_t)(z - q) * h + (y - q)) * h + (x - q)]
-                             : (double)rho_child[((size_t)z * N + y) * N + x];
+                    s += cov ? restr_child[((size_t)(z - q) * h + (y - q)) * h + (x - q)]
+                             : rho_child[((size_t)z * N + y) * N + x];
                 }
-        out[i] = (TIN)(s * 0.125);
+        out[i] = s * TIN(0.125);
     }
 }
 
@@ -37,7 +46,7 @@ cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* rest
     const int n = (N / 2) * (N / 2) * (N / 2);
     const int blocks = (n + 255) / 256;
     ProfScope ps(sizeof(TIN) == 4 ? "restrict_f32" : "restrict_f64", 1, s);
-    k_restrict<TIN><<<blocks, 256, 0, s>>>(rho_child, restr_child, restr_out, N);
+    k_restrict<TIN><<<blocks, 256, 0, s>>>(rho_child, restr_child, restr_out, ilog2(N));
     count_launches(1);
     return cudaGetLastError();
 }
@@ -120,54 +129,71 @@ cudaError_t run_to_float(const double* in, float* out, size_t n, cudaStream_t s)
 // centre i sits at level-k fractional index
 //   u = N/2 - N/(2r) + (i + 1/2)/r - 1/2,  r = 2^(n-k),
 // i.e. 2r u = (N - 1)(r - 1) + 2i, so the stencil corner and weight follow in
-// integer arithmetic and the weights are exact.  Each interpolated term is
-// formed in T; the per-cell sum over levels is accumulated in double.
+// integer arithmetic (shifts: N and r are powers of two) and the weights are
+// exact.  Each interpolated term is formed in T; the per-cell sum over levels
+// is accumulated in double.
 template <typename T>
-__device__ __forceinline__ void axis_stencil(int N, int r, int i, int& i0, T& t) {
-    const int num = (N - 1) * (r - 1) + 2 * i;
-    i0 = num / (2 * r);
-    t = (T)(num - i0 * 2 * r) / (T)(2 * r);
+__device__ __forceinline__ void axis_stencil(int N, int lgr, int i, int& i0, T& t) {
+    const int num = (N - 1) * ((1 << lgr) - 1) + 2 * i;
+    i0 = num >> (lgr + 1);
+    t = (T)(num & ((2 << lgr) - 1)) * ((T)1 / (T)(2 << lgr));
 }
 
+// float -> double by re-biasing the exponent: exact for normal numbers; zero,
+// subnormals and non-finite values take the conversion instruction.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 template <typename T>
-__global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a) {
-    const int N = a.N;
-    const size_t N3 = (size_t)N * N * N;
+__global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
+    const int N = 1 << lgN;
+    const size_t N3 = (size_t)1 << (3 * lgN);
     const size_t total = N3 * a.levels;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
-        const int n = (int)(idx / N3);
-        const size_t cell = idx - (size_t)n * N3;
-        const int x = (int)(cell % N), y = (int)((cell / N) % N), z = (int)(cell / ((size_t)N * N));
-        double acc = (double)a.base[n][cell];
+        const int n = (int)(idx >> (3 * lgN));
+        const size_t cell = idx & (N3 - 1);
+        const int x = (int)(cell & (N - 1)), y = (int)((cell >> lgN) & (N - 1)),
+                  z = (int)(cell >> (2 * lgN));
+        double acc = widen(a.base[n][cell]);
         if (a.dbl[n]) {
             const int E = 2 * N;
             const T* d = a.dbl[n];
-            double s = 0.0;
+            T s = T(0);
+#pragma unroll
             for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
                 for (int dy = 0; dy < 2; ++dy) {
                     const T* row = d + ((size_t)(2 * z + dz) * E + (2 * y + dy)) * E + 2 * x;
-                    s += (double)row[0] + (double)row[1];
+                    s += row[0] + row[1];
                 }
-            acc += 0.125 * s;
+            acc += widen(s * T(0.125));
         }
         for (int k = 0; k < n; ++k) {
-            const int r = 1 << (n - k);
+            const int lgr = n - k;
             int iz, iy, ix;
             T tz, ty, tx;
-            axis_stencil<T>(N, r, z, iz, tz);
-            axis_stencil<T>(N, r, y, iy, ty);
-            axis_stencil<T>(N, r, x, ix, tx);
+            axis_stencil<T>(N, lgr, z, iz, tz);
+            axis_stencil<T>(N, lgr, y, iy, ty);
+            axis_stencil<T>(N, lgr, x, ix, tx);
             const int o = a.interp_origin[k], E = a.interp_extent[k];
             const T* src = a.interp[k] + ((size_t)(iz - o) * E + (iy - o)) * E + (ix - o);
             const size_t sz = (size_t)E * E, sy = E;
-            const T c00 = src[0] * (T(1) - tx) + src[1] * tx;
-            const T c01 = src[sy] * (T(1) - tx) + src[sy + 1] * tx;
-            const T c10 = src[sz] * (T(1) - tx) + src[sz + 1] * tx;
-            const T c11 = src[sz + sy] * (T(1) - tx) + src[sz + sy + 1] * tx;
-            const T c0 = c00 * (T(1) - ty) + c01 * ty;
-            const T c1 = c10 * (T(1) - ty) + c11 * ty;
-            acc += (double)(c0 * (T(1) - tz) + c1 * tz);
+            const T c00 = src[0] + tx * (src[1] - src[0]);
+            const T c01 = src[sy] + tx * (src[sy + 1] - src[sy]);
+            const T c10 = src[sz] + tx * (src[sz + 1] - src[sz]);
+            const T c11 = src[sz + sy] + tx * (src[sz + sy + 1] - src[sz + sy]);
+            const T c0 = c00 + ty * (c01 - c00);
+            const T c1 = c10 + ty * (c11 - c10);
+            acc += widen(c0 + tz * (c1 - c0));
         }
         a.phi[idx] = acc;
     }
@@ -179,7 +205,7 @@ cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
     size_t blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     ProfScope ps(sizeof(T) == 4 ? "assemble_f32" : "assemble_f64", a.levels, s);
-    k_assemble<T><<<(int)blocks, 256, 0, s>>>(a);
+    k_assemble<T><<<(int)blocks, 256, 0, s>>>(a, ilog2(a.N));
     count_launches(1);
     return cudaGetLastError();
 }
