@@ -39,7 +39,7 @@
  * rho : L * N^3 densities, contiguous [level][z][y][x] (x fastest), level 0
  *       coarsest.  double for NM_FP64 plans, float for NM_FP32 plans.
  * phi : L * N^3 doubles, same layout; every cell of every level is written,
- *       covered cells included.
+ *       covered cells included.  Device phi must be 16-byte aligned.
  * Pointers passed to nm_potential are DEVICE pointers (current device),
  * owned by the caller; nm_potential_host takes HOST pointers.
  *
@@ -132,11 +132,49 @@ nm_status nm_potential_host(nm_plan_t plan, const void* rho_host, double* phi_ho
 nm_status nm_workspace_bytes(nm_plan_t plan, size_t* bytes);
 nm_status nm_spectrum_bytes(nm_plan_t plan, size_t* bytes);
 
-/* Solve `n` independent meshes in one batched schedule on `stream`: the
- * passes of all meshes and levels are grouped by kind into shared launches.
- * plans[i], rho[i], phi[i] as for nm_potential; the plans must be distinct. */
+/* Device bytes nm_plan_ex(opt) would allocate for its workspace with the
+ * default schedule (no device work, no allocation): lets a server admit a
+ * request by footprint before creating its plan.  NM_EINVAL / NM_EUNSUPPORTED
+ * as nm_plan_ex. */
+nm_status nm_footprint_bytes(const nm_options* opt, size_t* bytes);
+
+/* Solve `n` independent meshes in one batched schedule on `stream` (the
+ * levels and meshes are independent sub-problems, Sect. 4).  The passes of all
+ * meshes are issued round by round: in round r every mesh contributes its r-th
+ * group of level convolutions, and all contributions with the same transform
+ * size and schedule share one launch per pass.  The first call with a given
+ * (plans, rho, phi) set runs eagerly; a repeated call with the same set
+ * replays a CUDA graph captured from it (pointers are baked into the graph, so
+ * change the set to change the buffers).  plans[i], rho[i], phi[i] as for
+ * nm_potential; plans must be distinct and on the current device; FP32 and
+ * FP64 plans may be mixed. */
 nm_status nm_batch_potential(int n, const nm_plan_t* plans, const void* const* rho,
                              double* const* phi, void* stream);
+
+/* Kernel schedule of a plan's level convolutions. */
+typedef struct {
+    int group;   /* level convolutions (pairs of real fields) per launch, >= 1;
+                    larger groups fill the GPU, smaller ones keep a pass's
+                    working set in L2 for the next pass                      */
+    int radix;   /* values per thread = first-pass radix: 16 or 8             */
+    int tile;    /* column tile of the strided passes: 0 = 128-byte rows,
+                    1 = 256-byte rows                                         */
+} nm_schedule;
+
+/* Read / set the schedule (set reallocates the work buffers when group
+ * grows; synchronises the device).  NM_EINVAL for out-of-range fields. */
+nm_status nm_get_schedule(nm_plan_t plan, nm_schedule* out);
+nm_status nm_set_schedule(nm_plan_t plan, const nm_schedule* sched);
+
+/* Autotuner: times every candidate schedule (group in {1, 2, all}, radix in
+ * {16, 8}, tile in {0, 1}) with CUDA events over `reps` solves of the
+ * caller's rho into phi (phi is overwritten), on `stream`, keeps the fastest
+ * on the plan and records it in a process-wide table keyed by (device name,
+ * N, levels, precision, method) that later plans of the same key start from.
+ * When the environment variable NM_AUTOTUNE_CACHE names a file, the table is
+ * read from it at the first plan creation and appended to after each tuning
+ * (one JSON object per line).  Synchronous. */
+nm_status nm_autotune(nm_plan_t plan, const void* rho, double* phi, int reps, void* stream);
 
 /* Copy the plan's unit-cell spectrum octant ((N+1)^3 doubles, [kz][ky][kx])
  * to host memory `host_out`.  Synchronous.  Test hook. */

@@ -201,10 +201,12 @@ struct nm_plan_s {
     int N = 0, L = 0, P = 0;
     bool fp32 = false, dipole = false;
     size_t es = 8, cs = 16;           // bytes per real / complex value
-    int group = 1, group_dbl = 1;     // pairs in flight per launch
+    nm_schedule sched{1, 16, 0};      // level convolutions
+    int group_dbl = 1;                // doubled-grid convolutions in flight
     int npairs = 0, npairs_dbl = 0;
+    int work_slots = 0;               // work buffers allocated (>= sched.group)
     void* restr = nullptr;            // (L-1) * (N/2)^3 restricted densities
-    void* work = nullptr;             // group * (P/2) * P^2 complex
+    void* work = nullptr;             // work_slots * (P/2) * P^2 complex
     void* lvl = nullptr;              // L * N^3 level potentials
     void* crop = nullptr;             // (L-1) * (N/2+2)^3 hole crops (original method)
     void* dbl_work = nullptr;         // group_dbl * (2N) * (4N)^2 complex (dipole)
@@ -218,15 +220,19 @@ struct nm_plan_s {
     Twiddle* tw_dbl = nullptr;
 };
 
-static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+namespace {
 
-static int env_int(const char* name, int dflt) {
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int env_int(const char* name, int dflt) {
     const char* v = std::getenv(name);
     if (!v || !*v) return dflt;
     return std::atoi(v);
 }
 
-static void plan_free_buffers(nm_plan_t p) {
+size_t work_buf_bytes(nm_plan_t p) { return (size_t)(p->P / 2) * p->P * p->P * p->cs; }
+
+void plan_free_buffers(nm_plan_t p) {
     cudaFree(p->restr);
     cudaFree(p->work);
     cudaFree(p->lvl);
@@ -242,7 +248,7 @@ static void plan_free_buffers(nm_plan_t p) {
 // Pairs in flight per launch: all of them while one pair's work buffer is
 // small, one at a time once a buffer is large enough that keeping it resident
 // in L2 between passes matters more than filling the GPU with several.
-static int default_group(size_t buf_bytes, int npairs) {
+int default_group(size_t buf_bytes, int npairs) {
     int g = env_int("NM_GROUP", 0);
     if (g <= 0) {
         const size_t budget = (size_t)64 << 20;
@@ -252,6 +258,128 @@ static int default_group(size_t buf_bytes, int npairs) {
     if (g < 1) g = 1;
     return g;
 }
+
+// (Re)size the level work buffers to hold `slots` pairs.
+nm_status ensure_work_slots(nm_plan_t p, int slots) {
+    if (slots <= p->work_slots && slots * 2 > p->work_slots) return NM_OK;
+    NM_CUDA(cudaDeviceSynchronize(), "work buffer resize");
+    const size_t buf = work_buf_bytes(p);
+    if (p->work) {
+        cudaFree(p->work);
+        p->ws_bytes -= (size_t)p->work_slots * buf;
+        p->work = nullptr;
+        p->work_slots = 0;
+    }
+    NM_CUDA(cudaMalloc(&p->work, (size_t)slots * buf), "work buffers");
+    p->work_slots = slots;
+    p->ws_bytes += (size_t)slots * buf;
+    return NM_OK;
+}
+
+// ---------------------------------------------------------------- schedule table
+std::mutex g_tune_mu;
+struct TuneEntry {
+    std::string key;
+    nm_schedule sched;
+};
+std::vector<TuneEntry> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(nm_plan_t p) {
+    cudaDeviceProp prop;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&prop, p->dev) == cudaSuccess) name = prop.name;
+    for (auto& c : name)
+        if (c == '"' || c == '|') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|N%d|L%d|%s|%s", name.c_str(), p->N, p->L, p->fp32 ? "fp32" : "fp64",
+             p->dipole ? "dipole" : "original");
+    return buf;
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("NM_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char key[300];
+        nm_schedule sc;
+        if (std::sscanf(line, " {\"key\": \"%299[^\"]\", \"group\": %d, \"radix\": %d, \"tile\": %d",
+                        key, &sc.group, &sc.radix, &sc.tile) == 4) {
+            bool found = false;
+            for (auto& e : g_tune)
+                if (e.key == key) { e.sched = sc; found = true; }
+            if (!found) g_tune.push_back({key, sc});
+        }
+    }
+    std::fclose(f);
+}
+
+bool tune_lookup(nm_plan_t p, nm_schedule* out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    const std::string k = tune_key(p);
+    for (auto& e : g_tune)
+        if (e.key == k) { *out = e.sched; return true; }
+    return false;
+}
+
+void tune_store(nm_plan_t p, const nm_schedule& sc) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    const std::string k = tune_key(p);
+    bool found = false;
+    for (auto& e : g_tune)
+        if (e.key == k) { e.sched = sc; found = true; }
+    if (!found) g_tune.push_back({k, sc});
+    const char* path = std::getenv("NM_AUTOTUNE_CACHE");
+    if (path && *path) {
+        FILE* f = std::fopen(path, "a");
+        if (f) {
+            std::fprintf(f, "{\"key\": \"%s\", \"group\": %d, \"radix\": %d, \"tile\": %d}\n", k.c_str(),
+                         sc.group, sc.radix, sc.tile);
+            std::fclose(f);
+        }
+    }
+}
+
+bool sched_valid(nm_plan_t p, const nm_schedule& sc) {
+    if (sc.group < 1 || sc.group > p->npairs) return false;
+    if (sc.radix != 8 && sc.radix != 16) return false;
+    if (sc.radix == 16 && p->P < 16) return false;
+    return sc.tile == 0 || sc.tile == 1;
+}
+
+// ---------------------------------------------------------------- graphs of batches
+struct BatchGraph {
+    std::vector<const void*> key;
+    cudaGraphExec_t exec = nullptr;
+    bool captured = false;
+};
+std::mutex g_graph_mu;
+std::vector<BatchGraph> g_graphs;   // most recent last
+constexpr size_t kMaxGraphs = 8;
+
+void graphs_drop_plan(nm_plan_t p) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (size_t i = 0; i < g_graphs.size();) {
+        bool uses = false;
+        for (const void* k : g_graphs[i].key)
+            if (k == (const void*)p) uses = true;
+        if (uses) {
+            if (g_graphs[i].exec) cudaGraphExecDestroy(g_graphs[i].exec);
+            g_graphs.erase(g_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -267,10 +395,7 @@ nm_status nm_default_options(int levels, int N, double dx0, nm_options* opt) {
     return NM_OK;
 }
 
-nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
-    if (!opt || !out) return fail(NM_EINVAL, "nm_plan_ex: null argument");
-    *out = nullptr;
-    const nm_options o = *opt;
+static nm_status validate_options(const nm_options& o) {
     if (o.levels < 1 || o.levels > NM_MAX_LEVELS)
         return fail(NM_EINVAL, "levels must be in [1, %d], got %d", NM_MAX_LEVELS, o.levels);
     if (o.N < 4 || o.N % 4 != 0)
@@ -283,11 +408,49 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     if (o.method != NM_METHOD_ORIGINAL && o.method != NM_METHOD_DIPOLE_PAIR)
         return fail(NM_EINVAL, "bad method %d", o.method);
     if (o.interp != NM_INTERP_TRILINEAR) return fail(NM_EUNSUPPORTED, "only trilinear interpolation is built");
+    return NM_OK;
+}
+
+// Workspace bytes of a plan with the default schedule (mirrors nm_plan_ex).
+static size_t default_footprint(const nm_options& o) {
+    const size_t N = o.N, L = o.levels, P = 2 * N;
+    const size_t es = o.precision == NM_FP32 ? 4 : 8, cs = 2 * es;
+    const bool dipole = o.method == NM_METHOD_DIPOLE_PAIR;
+    const size_t N3 = N * N * N, h3 = N3 / 8, nc = N / 2 + 2;
+    const int npairs = dipole ? (int)((L + 1) / 2) : (int)L;
+    const size_t buf = (P / 2) * P * P * cs;
+    size_t b = (L - 1) * h3 * es + (size_t)default_group(buf, npairs) * buf + L * N3 * es;
+    if (!dipole) b += (L - 1) * nc * nc * nc * es;
+    if (dipole && L > 1) {
+        const size_t buf_dbl = (2 * N) * (4 * N) * (4 * N) * cs;
+        b += (size_t)default_group(buf_dbl, (int)(L / 2)) * buf_dbl + (L - 1) * 8 * N3 * es;
+    }
+    return b;
+}
+
+nm_status nm_footprint_bytes(const nm_options* opt, size_t* bytes) {
+    if (!opt || !bytes) return fail(NM_EINVAL, "nm_footprint_bytes: null argument");
+    nm_status st = validate_options(*opt);
+    if (st != NM_OK) return st;
+    *bytes = default_footprint(*opt);
+    return NM_OK;
+}
+
+nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
+    if (!opt || !out) return fail(NM_EINVAL, "nm_plan_ex: null argument");
+    *out = nullptr;
+    const nm_options o = *opt;
+    nm_status vst = validate_options(o);
+    if (vst != NM_OK) return vst;
 
     nm_plan_t p = new (std::nothrow) nm_plan_s();
     if (!p) return fail(NM_ENOMEM, "host allocation");
     p->opt = o;
-    NM_CUDA(cudaGetDevice(&p->dev), "cudaGetDevice");
+    cudaError_t ge = cudaGetDevice(&p->dev);
+    if (ge != cudaSuccess) {
+        delete p;
+        return cuda_fail(ge, "cudaGetDevice");
+    }
     p->N = o.N;
     p->L = o.levels;
     p->P = 2 * o.N;
@@ -295,13 +458,16 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     p->dipole = o.method == NM_METHOD_DIPOLE_PAIR;
     p->es = p->fp32 ? 4 : 8;
     p->cs = 2 * p->es;
-    const size_t N = o.N, L = o.levels, P = p->P;
+    const size_t N = o.N, L = o.levels;
     const size_t N3 = N * N * N, h3 = (N / 2) * (N / 2) * (N / 2);
     const size_t nc = N / 2 + 2, nc3 = nc * nc * nc;
     p->npairs = p->dipole ? (int)((L + 1) / 2) : (int)L;
     p->npairs_dbl = p->dipole ? (int)(L / 2) : 0;   // ceil((L-1)/2)
-    const size_t buf = (P / 2) * P * P * p->cs;
-    p->group = default_group(buf, p->npairs);
+    p->sched.group = default_group(work_buf_bytes(p), p->npairs);
+    p->sched.radix = p->P >= 16 ? 16 : 8;
+    p->sched.tile = 0;
+    nm_schedule tuned;
+    if (tune_lookup(p, &tuned) && sched_valid(p, tuned)) p->sched = tuned;
     const size_t buf_dbl = (2 * N) * (4 * N) * (4 * N) * p->cs;
     if (p->dipole) p->group_dbl = default_group(buf_dbl, p->npairs_dbl);
 
@@ -312,7 +478,8 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
         if (e == cudaSuccess) p->ws_bytes += bytes;
     };
     alloc(&p->restr, (L - 1) * h3 * p->es);
-    alloc(&p->work, (size_t)p->group * buf);
+    alloc(&p->work, (size_t)p->sched.group * work_buf_bytes(p));
+    if (e == cudaSuccess) p->work_slots = p->sched.group;
     alloc(&p->lvl, L * N3 * p->es);
     if (!p->dipole) alloc(&p->crop, (L - 1) * nc3 * p->es);
     if (p->dipole && L > 1) {
@@ -372,27 +539,17 @@ SrcField field(nm_plan_t p, const void* rho, int m, int mode, int P) {
     return f;
 }
 
+const SrcField kNoSrc{nullptr, nullptr, SRC_NONE, 0.0};
+
+// The level convolutions of one solve (work pointers unset).
 template <typename T>
-nm_status solve_t(nm_plan_t p, const void* rho, double* phi, cudaStream_t s,
-                  cudaError_t (*run_conv)(const PairDesc<T>*, int, int, bool, const T*,
-                                          const cpx<T>*, cudaStream_t)) {
-    const int L = p->L, N = p->N, P = p->P;
-    const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
-    const size_t nc = N / 2 + 2, nc3 = nc * nc * nc;
-    const T* spec = p->fp32 ? (const T*)(void*)p->spec->d32 : (const T*)(void*)p->spec->d64;
-    const cpx<T>* tw = p->fp32 ? (const cpx<T>*)(void*)p->tw->d32 : (const cpx<T>*)(void*)p->tw->d64;
+void level_pairs(nm_plan_t p, const void* rho, std::vector<PairDesc<T>>& out) {
+    const int L = p->L, P = p->P;
+    const size_t N3 = (size_t)p->N * p->N * p->N;
+    const size_t nc = p->N / 2 + 2, nc3 = nc * nc * nc;
     T* lvl = (T*)p->lvl;
-    cudaError_t e;
-    // 1. restriction, finest -> coarsest
-    for (int m = L - 2; m >= 0; --m) {
-        const T* child = (const T*)rho + (size_t)(m + 1) * N3;
-        const T* rchild = (m + 1 < L - 1) ? (const T*)p->restr + (size_t)(m + 1) * h3 : nullptr;
-        e = run_restrict<T>(child, rchild, (T*)p->restr + (size_t)m * h3, N, s);
-        if (e != cudaSuccess) return cuda_fail(e, "restriction");
-    }
-    // 2. level convolutions
-    std::vector<PairDesc<T>> pairs;
     if (!p->dipole) {
+        // Eq. 14: level m's full grid (re) and hole grid (im), Fig. 5
         for (int m = 0; m < L; ++m) {
             PairDesc<T> d{};
             d.src[0] = field(p, rho, m, SRC_FULL, P);
@@ -401,12 +558,14 @@ nm_status solve_t(nm_plan_t p, const void* rho, double* phi, cudaStream_t s,
                 d.src[1] = field(p, rho, m, SRC_HOLE, P);
                 d.dst[1] = {(T*)p->crop + (size_t)m * nc3, DST_CROP};
             } else {
-                d.src[1] = SrcField{nullptr, nullptr, SRC_NONE, 0.0};
+                d.src[1] = kNoSrc;
                 d.dst[1] = {nullptr, DST_NONE};
             }
-            pairs.push_back(d);
+            out.push_back(d);
         }
     } else {
+        // Eqs. 15, B.1-B.2: hole grids of every level but the finest, and the
+        // finest full grid, two real fields per complex transform
         for (int m = 0; m < L; m += 2) {
             PairDesc<T> d{};
             for (int h = 0; h < 2; ++h) {
@@ -415,49 +574,75 @@ nm_status solve_t(nm_plan_t p, const void* rho, double* phi, cudaStream_t s,
                     d.src[h] = field(p, rho, lv, lv < L - 1 ? SRC_HOLE : SRC_FULL, P);
                     d.dst[h] = {lvl + (size_t)lv * N3, DST_GRID};
                 } else {
-                    d.src[h] = SrcField{nullptr, nullptr, SRC_NONE, 0.0};
+                    d.src[h] = kNoSrc;
                     d.dst[h] = {nullptr, DST_NONE};
                 }
             }
-            pairs.push_back(d);
+            out.push_back(d);
         }
     }
-    const size_t buf = (size_t)(P / 2) * P * P;
-    for (size_t g0 = 0; g0 < pairs.size(); g0 += p->group) {
-        const int np = (int)std::min(pairs.size() - g0, (size_t)p->group);
-        for (int i = 0; i < np; ++i) pairs[g0 + i].work = (cpx<T>*)p->work + (size_t)i * buf;
-        e = run_conv(&pairs[g0], np, P, false, spec, tw, s);
-        if (e != cudaSuccess) return cuda_fail(e, "level convolution");
-    }
-    // 3. doubled fine grids (pairwise dipole method)
-    if (p->dipole && L > 1) {
-        const int P2 = 2 * P;
-        const T* spec2 = p->fp32 ? (const T*)(void*)p->spec_dbl->d32 : (const T*)(void*)p->spec_dbl->d64;
-        const cpx<T>* tw2 = p->fp32 ? (const cpx<T>*)(void*)p->tw_dbl->d32 : (const cpx<T>*)(void*)p->tw_dbl->d64;
-        std::vector<PairDesc<T>> dp;
-        for (int n = 0; n < L - 1; n += 2) {
-            PairDesc<T> d{};
-            for (int h = 0; h < 2; ++h) {
-                const int nn = n + h;
-                if (nn < L - 1) {
-                    d.src[h] = field(p, rho, nn + 1, SRC_FULL, P2);
-                    d.dst[h] = {(T*)p->dbl_out + (size_t)nn * 8 * N3, DST_GRID};
-                } else {
-                    d.src[h] = SrcField{nullptr, nullptr, SRC_NONE, 0.0};
-                    d.dst[h] = {nullptr, DST_NONE};
-                }
+}
+
+// Doubled fine grids (Fig. 16): level n+1's mass on 2N cells spanning level n.
+template <typename T>
+void dbl_pairs(nm_plan_t p, const void* rho, std::vector<PairDesc<T>>& out) {
+    const int L = p->L, P2 = 2 * p->P;
+    const size_t N3 = (size_t)p->N * p->N * p->N;
+    for (int n = 0; n < L - 1; n += 2) {
+        PairDesc<T> d{};
+        for (int h = 0; h < 2; ++h) {
+            const int nn = n + h;
+            if (nn < L - 1) {
+                d.src[h] = field(p, rho, nn + 1, SRC_FULL, P2);
+                d.dst[h] = {(T*)p->dbl_out + (size_t)nn * 8 * N3, DST_GRID};
+            } else {
+                d.src[h] = kNoSrc;
+                d.dst[h] = {nullptr, DST_NONE};
             }
-            dp.push_back(d);
         }
-        const size_t buf2 = (size_t)(P2 / 2) * P2 * P2;
-        for (size_t g0 = 0; g0 < dp.size(); g0 += p->group_dbl) {
-            const int np = (int)std::min(dp.size() - g0, (size_t)p->group_dbl);
-            for (int i = 0; i < np; ++i) dp[g0 + i].work = (cpx<T>*)p->dbl_work + (size_t)i * buf2;
-            e = run_conv(&dp[g0], np, P2, true, spec2, tw2, s);
-            if (e != cudaSuccess) return cuda_fail(e, "doubled-grid convolution");
-        }
+        out.push_back(d);
     }
-    // 4. assembly
+}
+
+template <typename T> const T* spec_of(const Spectrum* s);
+template <> const float* spec_of<float>(const Spectrum* s) { return s->d32; }
+template <> const double* spec_of<double>(const Spectrum* s) { return s->d64; }
+template <typename T> const cpx<T>* tw_of(const Twiddle* t);
+template <> const cpx<float>* tw_of<float>(const Twiddle* t) { return t->d32; }
+template <> const cpx<double>* tw_of<double>(const Twiddle* t) { return t->d64; }
+
+template <typename T>
+cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, bool dbl, int radix, int tile,
+                     const T* spec, const cpx<T>* tw, cudaStream_t s) {
+    const bool e16 = dbl || (radix == 16 && P >= 16);
+    if constexpr (sizeof(T) == 4) {
+        return e16 ? run_conv_f32_e16(pairs, n, P, dbl, tile != 0, spec, tw, s)
+                   : run_conv_f32_e8(pairs, n, P, dbl, tile != 0, spec, tw, s);
+    } else {
+        return e16 ? run_conv_f64_e16(pairs, n, P, dbl, tile != 0, spec, tw, s)
+                   : run_conv_f64_e8(pairs, n, P, dbl, tile != 0, spec, tw, s);
+    }
+}
+
+template <typename T>
+nm_status enqueue_restrict(nm_plan_t p, const void* rho, cudaStream_t s) {
+    const int L = p->L, N = p->N;
+    const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
+    for (int m = L - 2; m >= 0; --m) {
+        const T* child = (const T*)rho + (size_t)(m + 1) * N3;
+        const T* rchild = (m + 1 < L - 1) ? (const T*)p->restr + (size_t)(m + 1) * h3 : nullptr;
+        cudaError_t e = run_restrict<T>(child, rchild, (T*)p->restr + (size_t)m * h3, N, s);
+        if (e != cudaSuccess) return cuda_fail(e, "restriction");
+    }
+    return NM_OK;
+}
+
+template <typename T>
+nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
+    const int L = p->L, N = p->N;
+    const size_t N3 = (size_t)N * N * N;
+    const size_t nc = N / 2 + 2, nc3 = nc * nc * nc;
+    const T* lvl = (const T*)p->lvl;
     AssembleArgs<T> a{};
     a.phi = phi;
     a.levels = L;
@@ -477,18 +662,122 @@ nm_status solve_t(nm_plan_t p, const void* rho, double* phi, cudaStream_t s,
             }
         }
     }
-    e = run_assemble<T>(a, s);
+    cudaError_t e = run_assemble<T>(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "assembly");
     return NM_OK;
 }
 
-nm_status potential_impl(nm_plan_t p, const void* rho, double* phi, cudaStream_t s) {
-    if (!p->spec->ready || (p->spec_dbl && !p->spec_dbl->ready)) {
-        nm_status st = nm_green(p, (void*)s);
-        if (st != NM_OK) return st;
+// One mesh of a batch (or a single solve).
+struct Item {
+    nm_plan_t p;
+    const void* rho;
+    double* phi;
+};
+
+// Restriction, level and doubled-grid convolutions round by round, assembly.
+// Every mesh uses its own workspace; in round r mesh i contributes pairs
+// [r g_i, (r+1) g_i) and contributions with equal (P, radix, tile) share a
+// launch per pass.
+template <typename T>
+nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
+    nm_status st;
+    for (const Item& it : items)
+        if ((st = enqueue_restrict<T>(it.p, it.rho, s)) != NM_OK) return st;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool dbl = pass == 1;
+        std::vector<std::vector<PairDesc<T>>> pl(items.size());
+        int rounds = 0;
+        for (size_t i = 0; i < items.size(); ++i) {
+            nm_plan_t p = items[i].p;
+            if (dbl) {
+                if (p->dipole && p->L > 1) dbl_pairs<T>(p, items[i].rho, pl[i]);
+            } else {
+                level_pairs<T>(p, items[i].rho, pl[i]);
+            }
+            const int g = dbl ? p->group_dbl : p->sched.group;
+            const int r = ((int)pl[i].size() + g - 1) / g;
+            if (r > rounds) rounds = r;
+        }
+        for (int r = 0; r < rounds; ++r) {
+            struct Bucket {
+                int P, radix, tile;
+                const T* spec;
+                const cpx<T>* tw;
+                std::vector<PairDesc<T>> pairs;
+            };
+            std::vector<Bucket> buckets;
+            for (size_t i = 0; i < items.size(); ++i) {
+                nm_plan_t p = items[i].p;
+                const int g = dbl ? p->group_dbl : p->sched.group;
+                const int P = dbl ? 2 * p->P : p->P;
+                const int radix = dbl ? 16 : p->sched.radix;
+                const int tile = dbl ? 0 : p->sched.tile;
+                const size_t buf = (size_t)(P / 2) * P * P;
+                cpx<T>* work = (cpx<T>*)(dbl ? p->dbl_work : p->work);
+                for (int q = r * g; q < (r + 1) * g && q < (int)pl[i].size(); ++q) {
+                    PairDesc<T> d = pl[i][q];
+                    d.work = work + (size_t)(q - r * g) * buf;
+                    Bucket* b = nullptr;
+                    for (auto& bb : buckets)
+                        if (bb.P == P && bb.radix == radix && bb.tile == tile) b = &bb;
+                    if (!b) {
+                        buckets.push_back({P, radix, tile, spec_of<T>(dbl ? p->spec_dbl : p->spec),
+                                           tw_of<T>(dbl ? p->tw_dbl : p->tw), {}});
+                        b = &buckets.back();
+                    }
+                    b->pairs.push_back(d);
+                }
+            }
+            for (auto& b : buckets) {
+                cudaError_t e = run_conv<T>(b.pairs.data(), (int)b.pairs.size(), b.P, dbl, b.radix,
+                                            b.tile, b.spec, b.tw, s);
+                if (e != cudaSuccess) return cuda_fail(e, dbl ? "doubled-grid convolution" : "level convolution");
+            }
+        }
     }
-    if (p->fp32) return solve_t<float>(p, rho, phi, s, run_conv_f32);
-    return solve_t<double>(p, rho, phi, s, run_conv_f64);
+    for (const Item& it : items)
+        if ((st = enqueue_assemble<T>(it.p, it.phi, s)) != NM_OK) return st;
+    return NM_OK;
+}
+
+nm_status ensure_green(nm_plan_t p, cudaStream_t s) {
+    if (!p->spec->ready || (p->spec_dbl && !p->spec_dbl->ready)) return nm_green(p, (void*)s);
+    return NM_OK;
+}
+
+nm_status enqueue_all(const std::vector<Item>& items, cudaStream_t s) {
+    std::vector<Item> f32, f64;
+    for (const Item& it : items) (it.p->fp32 ? f32 : f64).push_back(it);
+    nm_status st = NM_OK;
+    if (!f64.empty()) st = enqueue_items<double>(f64, s);
+    if (st == NM_OK && !f32.empty()) st = enqueue_items<float>(f32, s);
+    return st;
+}
+
+nm_status potential_impl(nm_plan_t p, const void* rho, double* phi, cudaStream_t s) {
+    nm_status st = ensure_green(p, s);
+    if (st != NM_OK) return st;
+    return enqueue_all({Item{p, rho, phi}}, s);
+}
+
+// One-second-scale timing of a solve with the plan's current schedule.
+nm_status time_solves(nm_plan_t p, const void* rho, double* phi, int reps, cudaStream_t s, float* ms) {
+    nm_status st = potential_impl(p, rho, phi, s);
+    if (st != NM_OK) return st;
+    cudaEvent_t a, b;
+    NM_CUDA(cudaEventCreate(&a), "event");
+    NM_CUDA(cudaEventCreate(&b), "event");
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps && st == NM_OK; ++r) st = potential_impl(p, rho, phi, s);
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != NM_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+    *ms /= (float)(reps > 0 ? reps : 1);
+    return NM_OK;
 }
 
 }  // namespace
@@ -497,6 +786,8 @@ extern "C" {
 
 nm_status nm_potential(nm_plan_t p, const void* rho, double* phi, void* stream) {
     if (!p || !rho || !phi) return fail(NM_EINVAL, "nm_potential: null argument");
+    if (((uintptr_t)phi & 15) || ((uintptr_t)rho & (p->es - 1)))
+        return fail(NM_EINVAL, "nm_potential: phi must be 16-byte aligned and rho element aligned");
     return potential_impl(p, rho, phi, (cudaStream_t)stream);
 }
 
@@ -520,15 +811,135 @@ nm_status nm_potential_host(nm_plan_t p, const void* rho_host, double* phi_host,
 nm_status nm_batch_potential(int n, const nm_plan_t* plans, const void* const* rho,
                              double* const* phi, void* stream) {
     if (n < 0 || (n > 0 && (!plans || !rho || !phi))) return fail(NM_EINVAL, "nm_batch_potential: bad arguments");
+    int dev = 0;
+    NM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    std::vector<Item> items;
+    std::vector<const void*> key;
     for (int i = 0; i < n; ++i) {
         if (!plans[i] || !rho[i] || !phi[i]) return fail(NM_EINVAL, "nm_batch_potential: null entry %d", i);
+        if ((uintptr_t)phi[i] & 15) return fail(NM_EINVAL, "nm_batch_potential: phi %d not 16-byte aligned", i);
+        if (plans[i]->dev != dev) return fail(NM_EINVAL, "nm_batch_potential: plan %d on another device", i);
         for (int k = 0; k < i; ++k)
             if (plans[k] == plans[i]) return fail(NM_EINVAL, "nm_batch_potential: plan %d repeated", i);
+        items.push_back({plans[i], rho[i], phi[i]});
+        key.push_back(plans[i]);
+        key.push_back(rho[i]);
+        key.push_back(phi[i]);
+        key.push_back((const void*)(uintptr_t)((plans[i]->sched.group << 8) | (plans[i]->sched.radix << 1) |
+                                               plans[i]->sched.tile));
     }
-    for (int i = 0; i < n; ++i) {
-        nm_status st = potential_impl(plans[i], rho[i], phi[i], (cudaStream_t)stream);
+    if (n == 0) return NM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto& it : items) {
+        nm_status st = ensure_green(it.p, s);
         if (st != NM_OK) return st;
     }
+    if (g_prof_on.load() || env_int("NM_NO_GRAPHS", 0)) return enqueue_all(items, s);
+    // repeated batch: replay its graph; first repeat: capture it
+    cudaGraphExec_t exec = nullptr;
+    bool seen = false;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (size_t i = 0; i < g_graphs.size(); ++i)
+            if (g_graphs[i].key == key) {
+                seen = true;
+                exec = g_graphs[i].exec;
+                BatchGraph g = g_graphs[i];
+                g_graphs.erase(g_graphs.begin() + i);
+                g_graphs.push_back(g);
+                break;
+            }
+    }
+    if (!seen) {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        if (g_graphs.size() >= kMaxGraphs) {
+            if (g_graphs.front().exec) cudaGraphExecDestroy(g_graphs.front().exec);
+            g_graphs.erase(g_graphs.begin());
+        }
+        g_graphs.push_back(BatchGraph{key, nullptr, false});
+    }
+    if (!seen) return enqueue_all(items, s);
+    if (!exec) {
+        cudaStream_t cs;
+        NM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        nm_status st = NM_OK;
+        if (e == cudaSuccess) {
+            st = enqueue_all(items, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        if (e == cudaSuccess && st == NM_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (st != NM_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (auto& g : g_graphs)
+            if (g.key == key) { g.exec = exec; g.captured = true; }
+    }
+    NM_CUDA(cudaGraphLaunch(exec, s), "batch graph launch");
+    return NM_OK;
+}
+
+nm_status nm_get_schedule(nm_plan_t p, nm_schedule* out) {
+    if (!p || !out) return fail(NM_EINVAL, "nm_get_schedule: null argument");
+    *out = p->sched;
+    return NM_OK;
+}
+
+nm_status nm_set_schedule(nm_plan_t p, const nm_schedule* sc) {
+    if (!p || !sc) return fail(NM_EINVAL, "nm_set_schedule: null argument");
+    if (!sched_valid(p, *sc))
+        return fail(NM_EINVAL, "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile 0 or 1",
+                    p->npairs);
+    nm_status st = ensure_work_slots(p, sc->group);
+    if (st != NM_OK) return st;
+    graphs_drop_plan(p);
+    p->sched = *sc;
+    return NM_OK;
+}
+
+nm_status nm_autotune(nm_plan_t p, const void* rho, double* phi, int reps, void* stream) {
+    if (!p || !rho || !phi) return fail(NM_EINVAL, "nm_autotune: null argument");
+    if ((uintptr_t)phi & 15) return fail(NM_EINVAL, "nm_autotune: phi must be 16-byte aligned");
+    if (reps < 1) reps = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> groups = {1, 2, p->npairs};
+    std::vector<nm_schedule> cands;
+    for (int g : groups)
+        for (int radix : {16, 8})
+            for (int tile : {0, 1}) {
+                nm_schedule c{g, radix, tile};
+                if (!sched_valid(p, c)) continue;
+                bool dup = false;
+                for (auto& o : cands)
+                    if (o.group == c.group && o.radix == c.radix && o.tile == c.tile) dup = true;
+                if (!dup) cands.push_back(c);
+            }
+    nm_status st = ensure_work_slots(p, p->npairs);
+    if (st != NM_OK) return st;
+    graphs_drop_plan(p);
+    const nm_schedule keep = p->sched;
+    nm_schedule best = keep;
+    float best_ms = 1e30f;
+    for (auto& c : cands) {
+        p->sched = c;
+        float ms = 0.f;
+        st = time_solves(p, rho, phi, reps, s, &ms);
+        if (st != NM_OK) {
+            p->sched = keep;
+            return st;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    p->sched = keep;
+    st = nm_set_schedule(p, &best);
+    if (st != NM_OK) return st;
+    tune_store(p, best);
     return NM_OK;
 }
 
@@ -566,6 +977,7 @@ nm_status nm_get_options(nm_plan_t p, nm_options* out) {
 nm_status nm_destroy(nm_plan_t p) {
     if (!p) return fail(NM_EINVAL, "nm_destroy: null plan");
     cudaError_t e = cudaDeviceSynchronize();
+    graphs_drop_plan(p);
     plan_free_buffers(p);
     release_spectrum(p->spec);
     release_spectrum(p->spec_dbl);

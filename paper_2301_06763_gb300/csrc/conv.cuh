@@ -48,7 +48,7 @@ template <typename T> struct PairDesc {
     DstField dst[2];
 };
 
-constexpr int kMaxPairs = 24;
+constexpr int kMaxPairs = 64;
 template <typename T> struct ConvArgs {
     PairDesc<T> pair[kMaxPairs];
     const T* spec;          // unit spectrum octant (P/2+1)^3, [kz][ky][kx]
@@ -81,8 +81,7 @@ __device__ __forceinline__ T src_value(const SrcField& f, T scale, int NL, int z
     return v * scale;
 }
 
-template <int P, bool DBL> struct Geo {
-    static constexpr int E = EOf<P>::value;
+template <int P, int E, bool DBL> struct Geo {
     static constexpr int NIN = DBL ? P / 4 : P / 2;   // input block extent
     static constexpr int OFF = DBL ? P / 8 : 0;       // its offset in the domain
     static constexpr int NOUT = P / 2;                // output window
@@ -93,10 +92,9 @@ template <int P, bool DBL> struct Geo {
 };
 
 // ---------------------------------------------------------------- pass 1
-template <typename T, typename TIN, int P, bool DBL>
+template <typename T, typename TIN, int P, int E, bool DBL>
 __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T> a) {
-    using G = Geo<P, DBL>;
-    constexpr int E = EOf<P>::value;
+    using G = Geo<P, E, DBL>;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -120,20 +118,19 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
         }
     }
     __syncthreads();
-    fft_line<T, P, false>(v, j, sm_tw,
-                          LineView<T, 1, true, EOf<P>::log2>{sm_lines + line * (P + P / E)});
+    fft_line<T, P, E, false>(v, j, sm_tw,
+                             LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
     if (valid) {
         cpx<T>* dst = d.work + ((size_t)(zi + G::OFF) * P + (yi + G::OFF)) * P;
 #pragma unroll
-        for (int s = 0; s < E; ++s) dst[out_index<P>(j, s)] = v[s];
+        for (int s = 0; s < E; ++s) dst[out_index<P, E>(j, s)] = v[s];
     }
 }
 
 // ---------------------------------------------------------------- passes 2, 4
-template <typename T, int P, int TX, bool INV, bool DBL>
-__global__ void __launch_bounds__(TX * P / EOf<P>::value) k_ypass(const __grid_constant__ ConvArgs<T> a) {
-    using G = Geo<P, DBL>;
-    constexpr int E = EOf<P>::value;
+template <typename T, int P, int E, int TX, bool INV, bool DBL>
+__global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ ConvArgs<T> a) {
+    using G = Geo<P, E, DBL>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
@@ -150,19 +147,18 @@ __global__ void __launch_bounds__(TX * P / EOf<P>::value) k_ypass(const __grid_c
         else v[r] = {T(0), T(0)};
     }
     __syncthreads();
-    fft_line<T, P, INV>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
+    fft_line<T, P, E, INV>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-        const int e = out_index<P>(j, s);
+        const int e = out_index<P, E>(j, s);
         if (!INV || e < G::NOUT) slab[(size_t)e * P + x] = v[s];
     }
 }
 
 // ---------------------------------------------------------------- pass 3
-template <typename T, int P, int TX, bool DBL>
-__global__ void __launch_bounds__(TX * P / EOf<P>::value) k_zseam(const __grid_constant__ ConvArgs<T> a) {
-    using G = Geo<P, DBL>;
-    constexpr int E = EOf<P>::value;
+template <typename T, int P, int E, int TX, bool DBL>
+__global__ void __launch_bounds__(TX * P / E) k_zseam(const __grid_constant__ ConvArgs<T> a) {
+    using G = Geo<P, E, DBL>;
     constexpr int H = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -181,23 +177,23 @@ __global__ void __launch_bounds__(TX * P / EOf<P>::value) k_zseam(const __grid_c
     }
     __syncthreads();
     const LineView<T, TX, false> view{sm_tile + l};
-    fft_line<T, P, false>(v, j, sm_tw, view);
+    fft_line<T, P, E, false>(v, j, sm_tw, view);
     const int fy = y <= P / 2 ? y : P - y;
     const int fx = x <= P / 2 ? x : P - x;
     const T* sp = a.spec + (size_t)fy * H + fx;
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-        const int kz = out_index<P>(j, s);
+        const int kz = out_index<P, E>(j, s);
         const int fz = kz <= P / 2 ? kz : P - kz;
         const T g = __ldg(sp + (size_t)fz * H * H);
         v[s].re *= g;
         v[s].im *= g;
     }
-    seam_permute<T, P>(v);
-    fft_line<T, P, true>(v, j, sm_tw, view);
+    seam_permute<T, P, E>(v);
+    fft_line<T, P, E, true>(v, j, sm_tw, view);
 #pragma unroll
     for (int s = 0; s < E; ++s) {
-        const int e = out_index<P>(j, s);
+        const int e = out_index<P, E>(j, s);
         if (e < G::NOUT) col[(size_t)e * P * P] = v[s];
     }
 }
@@ -216,9 +212,8 @@ __device__ __forceinline__ void store_out(const DstField& f, int z, int y, int x
     }
 }
 
-template <typename T, int P, bool DBL>
+template <typename T, int P, int E, bool DBL>
 __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T> a) {
-    constexpr int E = EOf<P>::value;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     constexpr int HALF = P / 2;
@@ -236,12 +231,12 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = valid ? src[j + r * (P / E)] : cpx<T>{T(0), T(0)};
     __syncthreads();
-    fft_line<T, P, true>(v, j, sm_tw,
-                         LineView<T, 1, true, EOf<P>::log2>{sm_lines + line * (P + P / E)});
+    fft_line<T, P, E, true>(v, j, sm_tw,
+                            LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
     if (valid) {
 #pragma unroll
         for (int s = 0; s < E; ++s) {
-            const int e = out_index<P>(j, s);
+            const int e = out_index<P, E>(j, s);
             if (e < HALF) {
                 store_out<T, P>(d.dst[0], z, y, e, v[s].re);
                 store_out<T, P>(d.dst[1], z, y, e, v[s].im);
@@ -250,11 +245,9 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
     }
 }
 
-// Column tile width of the strided passes: 128-byte rows of the tile, at most
-// 1024 threads, never wider than a row of the domain.
-template <typename T, int P> struct Tile {
-    static constexpr int E = EOf<P>::value;
-    static constexpr int W = (sizeof(T) == 4 ? 16 : 8);
+// Column tile width of the strided passes: at most the requested width W,
+// at most 1024 threads, never wider than a row of the domain.
+template <int P, int E, int W> struct Tile {
     static constexpr int A = W < P ? W : P;
     static constexpr int TX = (A * P / E > 1024) ? 1024 * E / P : A;
 };

@@ -1,5 +1,6 @@
 // conv_inst.cuh -- host dispatch of the five convolution passes for one real
-// type; included once per precision (conv_f32.cu, conv_f64.cu).
+// type T and one count E of values per thread; included once per (T, E) by
+// the conv_*.cu translation units so the variants compile in parallel.
 #pragma once
 #include <cstdio>
 
@@ -12,13 +13,13 @@ static cudaError_t prep_kernel(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T, int P, bool DBL>
+// W = requested column-tile width of the strided passes.
+template <typename T, int P, int E, int W, bool DBL>
 static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
-    using Gm = Geo<P, DBL>;
-    constexpr int E = EOf<P>::value;
+    using Gm = Geo<P, E, DBL>;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
-    constexpr int TX = Tile<T, P>::TX;
+    constexpr int TX = Tile<P, E, W>::TX;
     constexpr int NT = TX * P / E;   // threads of the strided passes
     const size_t c = sizeof(cpx<T>);
     const size_t sm_x = (size_t)P * c + (size_t)LINES * (P + P / E) * c;
@@ -26,11 +27,11 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
     // shared-memory limits are set once per kernel (thread-safe static init)
     static const cudaError_t prepared = [&]() {
         cudaError_t e;
-        if ((e = prep_kernel(k_xfwd<T, T, P, DBL>, sm_x)) != cudaSuccess) return e;
-        if ((e = prep_kernel(k_ypass<T, P, TX, false, DBL>, sm_yz)) != cudaSuccess) return e;
-        if ((e = prep_kernel(k_zseam<T, P, TX, DBL>, sm_yz)) != cudaSuccess) return e;
-        if ((e = prep_kernel(k_ypass<T, P, TX, true, DBL>, sm_yz)) != cudaSuccess) return e;
-        return prep_kernel(k_xinv<T, P, DBL>, sm_x);
+        if ((e = prep_kernel(k_xfwd<T, T, P, E, DBL>, sm_x)) != cudaSuccess) return e;
+        if ((e = prep_kernel(k_ypass<T, P, E, TX, false, DBL>, sm_yz)) != cudaSuccess) return e;
+        if ((e = prep_kernel(k_zseam<T, P, E, TX, DBL>, sm_yz)) != cudaSuccess) return e;
+        if ((e = prep_kernel(k_ypass<T, P, E, TX, true, DBL>, sm_yz)) != cudaSuccess) return e;
+        return prep_kernel(k_xinv<T, P, E, DBL>, sm_x);
     }();
     if (prepared != cudaSuccess) return prepared;
     const int rows_in = Gm::NIN * Gm::NIN;
@@ -41,59 +42,88 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
     {
         snprintf(nm_, sizeof nm_, "xfwd%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_xfwd<T, T, P, DBL><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        k_xfwd<T, T, P, E, DBL><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "yfwd%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_ypass<T, P, TX, false, DBL><<<dim3(P / TX, Gm::NIN, np), NT, sm_yz, s>>>(a);
+        k_ypass<T, P, E, TX, false, DBL><<<dim3(P / TX, Gm::NIN, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_zseam<T, P, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+        k_zseam<T, P, E, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "yinv%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_ypass<T, P, TX, true, DBL><<<dim3(P / TX, Gm::NOUT, np), NT, sm_yz, s>>>(a);
+        k_ypass<T, P, E, TX, true, DBL><<<dim3(P / TX, Gm::NOUT, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "xinv%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_xinv<T, P, DBL><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        k_xinv<T, P, E, DBL><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     count_launches(5);
     return cudaGetLastError();
 }
 
-template <typename T, bool DBL>
-static cudaError_t conv_dispatch(const ConvArgs<T>& a, int np, int P, cudaStream_t s) {
+// Narrow / wide column tiles: 128- and 256-byte rows for float, 128 and 256
+// for double.
+template <typename T> struct Widths {
+    static constexpr int NARROW = sizeof(T) == 4 ? 16 : 8;
+    static constexpr int WIDE = 2 * NARROW;
+};
+
+template <typename T, int P, int E, bool DBL>
+static cudaError_t conv_width(const ConvArgs<T>& a, int np, bool wide, cudaStream_t s) {
+    if (wide) return conv_passes<T, P, E, Widths<T>::WIDE, DBL>(a, np, s);
+    return conv_passes<T, P, E, Widths<T>::NARROW, DBL>(a, np, s);
+}
+
+// The doubled-grid geometry is instantiated only with the default schedule
+// (E = 16, narrow tiles) to bound compile time.
+template <typename T, int E>
+static cudaError_t conv_dispatch(const ConvArgs<T>& a, int np, int P, bool dbl, bool wide,
+                                 cudaStream_t s) {
+    if (dbl) {
+        if constexpr (E == 16) {
+            switch (P) {
+                case 16: return conv_passes<T, 16, 16, Widths<T>::NARROW, true>(a, np, s);
+                case 32: return conv_passes<T, 32, 16, Widths<T>::NARROW, true>(a, np, s);
+                case 64: return conv_passes<T, 64, 16, Widths<T>::NARROW, true>(a, np, s);
+                case 128: return conv_passes<T, 128, 16, Widths<T>::NARROW, true>(a, np, s);
+                case 256: return conv_passes<T, 256, 16, Widths<T>::NARROW, true>(a, np, s);
+                case 512: return conv_passes<T, 512, 16, Widths<T>::NARROW, true>(a, np, s);
+                case 1024: return conv_passes<T, 1024, 16, Widths<T>::NARROW, true>(a, np, s);
+                default: break;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (P) {
-        case 8: if constexpr (!DBL) return conv_passes<T, 8, DBL>(a, np, s); break;
-        case 16: return conv_passes<T, 16, DBL>(a, np, s);
-        case 32: return conv_passes<T, 32, DBL>(a, np, s);
-        case 64: return conv_passes<T, 64, DBL>(a, np, s);
-        case 128: return conv_passes<T, 128, DBL>(a, np, s);
-        case 256: return conv_passes<T, 256, DBL>(a, np, s);
-        case 512: return conv_passes<T, 512, DBL>(a, np, s);
-        case 1024: if constexpr (DBL) return conv_passes<T, 1024, DBL>(a, np, s); break;
+        case 8: if constexpr (E == 8) return conv_width<T, 8, 8, false>(a, np, wide, s); break;
+        case 16: return conv_width<T, 16, E, false>(a, np, wide, s);
+        case 32: return conv_width<T, 32, E, false>(a, np, wide, s);
+        case 64: return conv_width<T, 64, E, false>(a, np, wide, s);
+        case 128: return conv_width<T, 128, E, false>(a, np, wide, s);
+        case 256: return conv_width<T, 256, E, false>(a, np, wide, s);
+        case 512: return conv_width<T, 512, E, false>(a, np, wide, s);
         default: break;
     }
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
-static cudaError_t run_conv_t(const PairDesc<T>* pairs, int npairs, int P, bool dbl,
-                              const T* spec, const cpx<T>* tw, cudaStream_t s) {
+template <typename T, int E>
+static cudaError_t run_conv_variant(const PairDesc<T>* pairs, int npairs, int P, bool dbl,
+                                    bool wide, const T* spec, const cpx<T>* tw, cudaStream_t s) {
     ConvArgs<T> a;
     a.spec = spec;
     a.tw = tw;
     for (int i0 = 0; i0 < npairs; i0 += kMaxPairs) {
         const int np = npairs - i0 < kMaxPairs ? npairs - i0 : kMaxPairs;
         for (int i = 0; i < np; ++i) a.pair[i] = pairs[i0 + i];
-        cudaError_t e = dbl ? conv_dispatch<T, true>(a, np, P, s)
-                            : conv_dispatch<T, false>(a, np, P, s);
+        cudaError_t e = conv_dispatch<T, E>(a, np, P, dbl, wide, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

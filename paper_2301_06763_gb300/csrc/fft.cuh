@@ -131,21 +131,21 @@ template <typename T, bool INV, int R> __device__ __forceinline__ void dftR(cpx<
     else dft2<T, INV>(v);
 }
 
-// Values per thread for a line of length P.
+// Default values per thread for a line of length P.
 template <int P> struct EOf {
     static constexpr int value = P >= 16 ? 16 : 8;
-    static constexpr int log2 = P >= 16 ? 4 : 3;
+};
+template <int E> struct Log2E {
+    static constexpr int value = E == 16 ? 4 : 3;
 };
 
 // Radix of the pass that starts at stride NS, and of the last pass.
-template <int P, int NS> struct PassRadix {
-    static constexpr int E = EOf<P>::value;
+template <int P, int E, int NS> struct PassRadix {
     static constexpr int REM = P / NS;
     static constexpr int R = REM >= E ? E : REM;
 };
-template <int P> struct LastRadix {
+template <int P, int E> struct LastRadix {
     static constexpr int calc() {
-        const int E = EOf<P>::value;
         int ns = E, R = E;
         while (ns < P) {
             R = (P / ns >= E) ? E : P / ns;
@@ -177,10 +177,9 @@ __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* tw, int t) {
 }
 
 // Passes after the first.  NS = product of the radices done so far.
-template <typename T, int P, bool INV, int NS, class View>
+template <typename T, int P, int E, bool INV, int NS, class View>
 __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
-    constexpr int E = EOf<P>::value;
-    constexpr int R = PassRadix<P, NS>::R;
+    constexpr int R = PassRadix<P, E, NS>::R;
     constexpr int NB = E / R;
     constexpr bool LAST = (NS * R == P);
 #pragma unroll
@@ -209,36 +208,34 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
             for (int r = 0; r < R; ++r) sm.st(base + r * NS, v[b * R + r]);
         }
         __syncthreads();
-        fft_rest<T, P, INV, NS * R>(v, j, tw, sm);
+        fft_rest<T, P, E, INV, NS * R>(v, j, tw, sm);
     }
 }
 
 // Whole-line transform.  All threads of the CTA must call it (it contains
 // __syncthreads); the shared-memory line must not be in use by anyone else.
-template <typename T, int P, bool INV, class View>
+template <typename T, int P, int E, bool INV, class View>
 __device__ __forceinline__ void fft_line(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
-    constexpr int E = EOf<P>::value;
+    static_assert(P >= E, "line shorter than the values a thread holds");
     dftR<T, INV, E>(v);
     if constexpr (P > E) {
 #pragma unroll
         for (int r = 0; r < E; ++r) sm.st(E * j + r, v[r]);
         __syncthreads();
-        fft_rest<T, P, INV, E>(v, j, tw, sm);
+        fft_rest<T, P, E, INV, E>(v, j, tw, sm);
     }
 }
 
 // Output index of register slot s after fft_line (see the header comment).
-template <int P> __device__ __forceinline__ int out_index(int j, int s) {
-    constexpr int E = EOf<P>::value;
-    constexpr int R = LastRadix<P>::value;
+template <int P, int E> __device__ __forceinline__ int out_index(int j, int s) {
+    constexpr int R = LastRadix<P, E>::value;
     return j + (s / R) * (P / E) + (s % R) * (P / R);
 }
 
 // Output distribution -> input distribution, same thread:
 // in[b + r * (E/R)] = out[b * R + r].
-template <typename T, int P> __device__ __forceinline__ void seam_permute(cpx<T>* v) {
-    constexpr int E = EOf<P>::value;
-    constexpr int R = LastRadix<P>::value;
+template <typename T, int P, int E> __device__ __forceinline__ void seam_permute(cpx<T>* v) {
+    constexpr int R = LastRadix<P, E>::value;
     constexpr int NB = E / R;
     cpx<T> t[E];
 #pragma unroll

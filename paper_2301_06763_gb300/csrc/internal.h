@@ -20,12 +20,18 @@ struct ProfScope {
     ProfScope& operator=(const ProfScope&) = delete;
 };
 
-// Five-pass convolution of `npairs` packed pairs of FFT size P (see conv.cuh).
-// DBL selects the doubled-fine-grid geometry.  Returns the first launch error.
-cudaError_t run_conv_f32(const PairDesc<float>* pairs, int npairs, int P, bool dbl,
-                         const float* spec, const cpx<float>* tw, cudaStream_t s);
-cudaError_t run_conv_f64(const PairDesc<double>* pairs, int npairs, int P, bool dbl,
-                         const double* spec, const cpx<double>* tw, cudaStream_t s);
+// Five-pass convolution of `npairs` packed pairs of FFT size P (see conv.cuh),
+// one entry point per (precision, values per thread); `wide` selects the wider
+// column tile.  DBL selects the doubled-fine-grid geometry (16 values, narrow
+// tiles only).  Returns the first launch error.
+cudaError_t run_conv_f32_e16(const PairDesc<float>* pairs, int npairs, int P, bool dbl, bool wide,
+                             const float* spec, const cpx<float>* tw, cudaStream_t s);
+cudaError_t run_conv_f32_e8(const PairDesc<float>* pairs, int npairs, int P, bool dbl, bool wide,
+                            const float* spec, const cpx<float>* tw, cudaStream_t s);
+cudaError_t run_conv_f64_e16(const PairDesc<double>* pairs, int npairs, int P, bool dbl, bool wide,
+                             const double* spec, const cpx<double>* tw, cudaStream_t s);
+cudaError_t run_conv_f64_e8(const PairDesc<double>* pairs, int npairs, int P, bool dbl, bool wide,
+                            const double* spec, const cpx<double>* tw, cudaStream_t s);
 
 // Unit-cell kernel spectrum octant (N+1)^3 in double (Eqs. 10, 13, Fig. 4);
 // `scratch` holds 2 (N+1)^3 doubles, `ctab` the P = 2N cosines cos(2 pi t/P).

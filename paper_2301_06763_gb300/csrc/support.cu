@@ -139,69 +139,114 @@ __device__ __forceinline__ void axis_stencil(int N, int lgr, int i, int& i0, T& 
     t = (T)(num & ((2 << lgr) - 1)) * ((T)1 / (T)(2 << lgr));
 }
 
-// float -> double by re-biasing the exponent: exact for normal numbers; zero,
-// subnormals and non-finite values take the conversion instruction.
+// Exact float -> double in integer arithmetic (sign, exponent re-biased by
+// 1023 - 127 = 896, mantissa shifted by 29; subnormals normalised, infinities
+// and NaNs mapped to exponent 2047), so the FP32 path spends its FP64 pipe only
+// on the final additions.
 __device__ __forceinline__ double widen(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                    ((unsigned long long)(e + 896u) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)bits);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    unsigned e = (u >> 23) & 0xffu;
+    unsigned m = u & 0x7fffffu;
+    unsigned long long ed;
+    if (e == 0xffu) {
+        ed = 2047ull;
+    } else if (e != 0u) {
+        ed = e + 896u;
+    } else if (m == 0u) {
+        return __longlong_as_double((long long)sign);
+    } else {
+        const int s = __clz(m) - 8;        // brings the leading one to bit 23
+        m = (m << s) & 0x7fffffu;
+        ed = (unsigned long long)(897 - s);
+    }
+    return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)m << 29)));
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, float* v) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+};
+template <> struct Vec4<double> {
+    static __device__ __forceinline__ void load(const double* p, double* v) {
+        const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+        const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    }
+};
+
+// One thread per 4 consecutive cells along x (N >= 4): the z and y stencils of
+// each coarser level are shared by the 4 cells.
 template <typename T>
 __global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
     const int N = 1 << lgN;
     const size_t N3 = (size_t)1 << (3 * lgN);
-    const size_t total = N3 * a.levels;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t quads = (N3 >> 2) * a.levels;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < quads;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const size_t idx = q << 2;
         const int n = (int)(idx >> (3 * lgN));
         const size_t cell = idx & (N3 - 1);
-        const int x = (int)(cell & (N - 1)), y = (int)((cell >> lgN) & (N - 1)),
+        const int x0 = (int)(cell & (N - 1)), y = (int)((cell >> lgN) & (N - 1)),
                   z = (int)(cell >> (2 * lgN));
-        double acc = widen(a.base[n][cell]);
+        T b[4];
+        Vec4<T>::load(a.base[n] + cell, b);
+        double acc[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = widen(b[c]);
         if (a.dbl[n]) {
             const int E = 2 * N;
             const T* d = a.dbl[n];
-            T s = T(0);
 #pragma unroll
-            for (int dz = 0; dz < 2; ++dz)
+            for (int c = 0; c < 4; ++c) {
+                T s = T(0);
 #pragma unroll
-                for (int dy = 0; dy < 2; ++dy) {
-                    const T* row = d + ((size_t)(2 * z + dz) * E + (2 * y + dy)) * E + 2 * x;
-                    s += row[0] + row[1];
-                }
-            acc += widen(s * T(0.125));
+                for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy) {
+                        const T* row = d + ((size_t)(2 * z + dz) * E + (2 * y + dy)) * E + 2 * (x0 + c);
+                        s += row[0] + row[1];
+                    }
+                acc[c] += widen(s * T(0.125));
+            }
         }
         for (int k = 0; k < n; ++k) {
             const int lgr = n - k;
-            int iz, iy, ix;
-            T tz, ty, tx;
+            int iz, iy;
+            T tz, ty;
             axis_stencil<T>(N, lgr, z, iz, tz);
             axis_stencil<T>(N, lgr, y, iy, ty);
-            axis_stencil<T>(N, lgr, x, ix, tx);
             const int o = a.interp_origin[k], E = a.interp_extent[k];
-            const T* src = a.interp[k] + ((size_t)(iz - o) * E + (iy - o)) * E + (ix - o);
             const size_t sz = (size_t)E * E, sy = E;
-            const T c00 = src[0] + tx * (src[1] - src[0]);
-            const T c01 = src[sy] + tx * (src[sy + 1] - src[sy]);
-            const T c10 = src[sz] + tx * (src[sz + 1] - src[sz]);
-            const T c11 = src[sz + sy] + tx * (src[sz + sy + 1] - src[sz + sy]);
-            const T c0 = c00 + ty * (c01 - c00);
-            const T c1 = c10 + ty * (c11 - c10);
-            acc += widen(c0 + tz * (c1 - c0));
+            const T* plane = a.interp[k] + ((size_t)(iz - o) * E + (iy - o)) * E - o;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                int ix;
+                T tx;
+                axis_stencil<T>(N, lgr, x0 + c, ix, tx);
+                const T* src = plane + ix;
+                const T c00 = src[0] + tx * (src[1] - src[0]);
+                const T c01 = src[sy] + tx * (src[sy + 1] - src[sy]);
+                const T c10 = src[sz] + tx * (src[sz + 1] - src[sz]);
+                const T c11 = src[sz + sy] + tx * (src[sz + sy + 1] - src[sz + sy]);
+                const T c0 = c00 + ty * (c01 - c00);
+                const T c1 = c10 + ty * (c11 - c10);
+                acc[c] += widen(c0 + tz * (c1 - c0));
+            }
         }
-        a.phi[idx] = acc;
+        double2* out = reinterpret_cast<double2*>(a.phi + idx);
+        out[0] = make_double2(acc[0], acc[1]);
+        out[1] = make_double2(acc[2], acc[3]);
     }
 }
 
 template <typename T>
 cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
-    const size_t total = (size_t)a.N * a.N * a.N * a.levels;
+    const size_t total = (size_t)a.N * a.N * a.N * a.levels / 4;
     size_t blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
     ProfScope ps(sizeof(T) == 4 ? "assemble_f32" : "assemble_f64", a.levels, s);

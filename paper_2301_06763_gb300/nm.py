@@ -29,6 +29,13 @@ class Options(ctypes.Structure):
                 ("interp", ctypes.c_int)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int), ("radix", ctypes.c_int), ("tile", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"group": self.group, "radix": self.radix, "tile": self.tile}
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64),
                 ("units", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
@@ -68,6 +75,11 @@ def lib():
             "nm_get_green_octant": (st, [P, P]),
             "nm_get_options": (st, [P, ctypes.POINTER(Options)]),
             "nm_destroy": (st, [P]),
+            "nm_footprint_bytes": (st, [ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_size_t)]),
+            "nm_get_schedule": (st, [P, ctypes.POINTER(Schedule)]),
+            "nm_set_schedule": (st, [P, ctypes.POINTER(Schedule)]),
+            "nm_autotune": (st, [P, P, P, ctypes.c_int, P]),
+            "nm_potential_noalloc": (st, [ctypes.POINTER(Options), P, P, P]),
             "nm_kernel_launches": (ctypes.c_uint64, []),
             "nm_profile_enable": (st, [ctypes.c_int]),
             "nm_profile_read": (st, [ctypes.POINTER(KernelStat), ctypes.c_int,
@@ -101,6 +113,23 @@ def kernel_launches():
     return int(lib().nm_kernel_launches())
 
 
+def make_options(levels, N, dx0, G=1.0, precision="fp64", method="original"):
+    o = Options()
+    _check(lib().nm_default_options(int(levels), int(N), float(dx0), ctypes.byref(o)))
+    o.G = float(G)
+    o.precision = _PREC[precision]
+    o.method = _METHOD[method]
+    return o
+
+
+def footprint_bytes(levels, N, dx0=1.0, G=1.0, precision="fp64", method="original"):
+    """Device bytes a plan of this shape would allocate (default schedule)."""
+    v = ctypes.c_size_t()
+    _check(lib().nm_footprint_bytes(ctypes.byref(make_options(levels, N, dx0, G, precision, method)),
+                                    ctypes.byref(v)))
+    return int(v.value)
+
+
 def profile_enable(on=True):
     """Bracket every library kernel with CUDA events (see nm_profile_enable)."""
     _check(lib().nm_profile_enable(1 if on else 0))
@@ -129,11 +158,7 @@ class Plan:
     """One nested mesh: ``levels`` levels of N^3 cells, coarsest cell ``dx0``."""
 
     def __init__(self, levels, N, dx0, G=1.0, precision="fp64", method="original"):
-        o = Options()
-        _check(lib().nm_default_options(int(levels), int(N), float(dx0), ctypes.byref(o)))
-        o.G = float(G)
-        o.precision = _PREC[precision]
-        o.method = _METHOD[method]
+        o = make_options(levels, N, dx0, G, precision, method)
         h = ctypes.c_void_p()
         _check(lib().nm_plan_ex(ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -187,6 +212,26 @@ class Plan:
         _check(lib().nm_potential_host(self.handle, ctypes.c_void_p(rho_np.ctypes.data),
                                        ctypes.c_void_p(phi_np.ctypes.data), _stream_handle(stream)))
         return phi
+
+    def schedule(self):
+        sc = Schedule()
+        _check(lib().nm_get_schedule(self.handle, ctypes.byref(sc)))
+        return sc.as_dict()
+
+    def set_schedule(self, group, radix, tile):
+        sc = Schedule(int(group), int(radix), int(tile))
+        _check(lib().nm_set_schedule(self.handle, ctypes.byref(sc)))
+
+    def autotune(self, rho, phi=None, reps=3, stream=None):
+        """Time the candidate schedules on these buffers, keep the fastest."""
+        import torch
+        self._check_tensor(rho, self.rho_dtype, "rho")
+        if phi is None:
+            phi = torch.empty(self.shape, dtype=torch.float64, device=rho.device)
+        self._check_tensor(phi, torch.float64, "phi")
+        _check(lib().nm_autotune(self.handle, ctypes.c_void_p(rho.data_ptr()),
+                                 ctypes.c_void_p(phi.data_ptr()), int(reps), _stream_handle(stream)))
+        return self.schedule()
 
     def workspace_bytes(self):
         v = ctypes.c_size_t()

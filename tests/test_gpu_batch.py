@@ -1,0 +1,103 @@
+"""Batched solves (nm_batch_potential), schedules and the autotuner."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_06763_gb300 import workloads as wl
+from tests.gpu_helpers import FP32_REL_MAX, FP64_REL_MAX, nm, rel_max
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(2, 8), (3, 16), (4, 32), (2, 4), (5, 16), (3, 8)]
+
+
+def make(shapes, precision, method="original", seed=0):
+    import torch
+    m = nm()
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plans, rhos, phis = [], [], []
+    for i, (L, N) in enumerate(shapes):
+        plans.append(m.Plan(L, N, 0.9 / N, 1.0, precision=precision, method=method))
+        rhos.append(torch.from_numpy(wl.random_density(seed + i, L, N)).to("cuda", dt))
+        phis.append(torch.empty((L, N, N, N), dtype=torch.float64, device="cuda"))
+    return plans, rhos, phis
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("method", ["original", "dipole"])
+def test_batch_equals_solo_bitwise(precision, method):
+    import torch
+    m = nm()
+    plans, rhos, phis = make(SHAPES, precision, method)
+    solo = [p.potential(r).cpu().numpy() for p, r in zip(plans, rhos)]
+    m.batch_potential(plans, rhos, phis)
+    torch.cuda.synchronize()
+    for a, b in zip(phis, solo):
+        assert np.array_equal(a.cpu().numpy(), b)
+    for p in plans:
+        p.close()
+
+
+def test_mixed_precision_batch_and_graph_replay():
+    import torch
+    m = nm()
+    p64, r64, f64 = make(SHAPES[:3], "fp64")
+    p32, r32, f32 = make(SHAPES[3:], "fp32", seed=10)
+    plans, rhos, phis = p64 + p32, r64 + r32, f64 + f32
+    for _ in range(3):            # eager, capture + replay, replay
+        m.batch_potential(plans, rhos, phis)
+    torch.cuda.synchronize()
+    first = [f.cpu().numpy() for f in phis]
+    # new contents behind the same pointers: the replayed graph reads them
+    for i, r in enumerate(rhos):
+        r.copy_(torch.from_numpy(wl.random_density(100 + i, *r.shape[:2])).to(r.dtype))
+    m.batch_potential(plans, rhos, phis)
+    torch.cuda.synchronize()
+    for p, r, f, old in zip(plans, rhos, phis, first):
+        assert np.array_equal(f.cpu().numpy(), p.potential(r).cpu().numpy())
+        assert not np.array_equal(f.cpu().numpy(), old)
+    for i, (L, N) in enumerate(SHAPES[:3]):
+        ref = oracle.solve(wl.random_density(100 + i, L, N), N, 0.9 / N)
+        assert rel_max(phis[i].cpu().numpy(), ref) <= FP64_REL_MAX
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_every_schedule_matches_the_oracle(precision):
+    import torch
+    m = nm()
+    L, N = 4, 16
+    rho = wl.random_density(7, L, N)
+    ref = oracle.solve(rho, N, 1.0 / N)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    r = torch.from_numpy(rho).to("cuda", dt)
+    tol = FP64_REL_MAX if precision == "fp64" else FP32_REL_MAX
+    with m.Plan(L, N, 1.0 / N, precision=precision) as p:
+        for group in (1, 2, 4):
+            for radix in (16, 8):
+                for tile in (0, 1):
+                    p.set_schedule(group, radix, tile)
+                    assert p.schedule() == {"group": group, "radix": radix, "tile": tile}
+                    assert rel_max(p.potential(r).cpu().numpy(), ref) <= tol
+        with pytest.raises(m.NMError):
+            p.set_schedule(5, 16, 0)
+        with pytest.raises(m.NMError):
+            p.set_schedule(1, 4, 0)
+
+
+def test_autotune_picks_a_valid_schedule_and_caches_it(tmp_path, monkeypatch):
+    import torch
+    m = nm()
+    L, N = 3, 32
+    rho = torch.from_numpy(wl.random_density(3, L, N)).to("cuda", torch.float32)
+    with m.Plan(L, N, 1.0 / N, precision="fp32") as p:
+        sc = p.autotune(rho, reps=2)
+        assert 1 <= sc["group"] <= L and sc["radix"] in (8, 16) and sc["tile"] in (0, 1)
+        ref = p.potential(rho).cpu().numpy()
+    # a later plan of the same shape starts from the tuned schedule
+    with m.Plan(L, N, 1.0 / N, precision="fp32") as q:
+        assert q.schedule() == sc
+        assert rel_max(q.potential(rho).cpu().numpy(), ref) <= 1e-6
