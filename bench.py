@@ -11,6 +11,8 @@ in HBM; the FP64 path, p50/p99, the end-to-end host-buffer rate, the roofline
 of the dominant kernel, the oracle's CPU rate and the clocks go alongside.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --mode batch    # 64 meshes, N in {32,64,128}, 2-8 levels, one batched call
+  python bench.py --mode serve    # Poisson request stream, rates swept, p50/p99 latency
 
 Under torchrun (N > 1) each rank solves its own copy of the workload (the
 meshes are independent: replicas, weak scaling); the timed region is bracketed
@@ -46,6 +48,11 @@ def parse():
     ap.add_argument("--N", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle CPU timing (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--mode", choices=["solve", "batch", "serve"], default="solve")
+    ap.add_argument("--rates", default="10,30,100,300,1000,2000")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="arrival window per rate (requests = rate x seconds, at most 2000)")
     return ap.parse_args()
 
 
@@ -278,6 +285,12 @@ def ours(args):
     p64 = nm.Plan(L, N, w.dx0, precision="fp64")
     p32.green()
     p64.green()
+    sched = {}
+    if not args.no_autotune:
+        sched["fp32"] = p32.autotune(rho32[0], phis[0], reps=3)
+        sched["fp64"] = p64.autotune(rho64[0], phis[0], reps=2)
+    else:
+        sched = {"fp32": p32.schedule(), "fp64": p64.schedule()}
     for i in range(max(args.warmup, 3)):
         p32.potential(rho32[i % NSETS], phis[i % NSETS])
         p64.potential(rho64[i % NSETS], phis[i % NSETS])
@@ -346,7 +359,8 @@ def ours(args):
                    "precision": "fp32 passes, fp64 spectrum and final sum", "method": "original",
                    "l2": "%d rotating rho/phi sets (%.0f MB > L2)" % (
                        NSETS, NSETS * (rho.size * 4 + rho.size * 8) / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "schedule": sched},
         "p50_ms": pct(per32, 50), "p99_ms": pct(per32, 99),
         "fp64": {"value": world * args.steps / (dev64_ms / 1e3), "unit": "solves/s",
                  "ms_per_step": dev64_ms / args.steps, "p50_ms": pct(per64, 50),
@@ -367,10 +381,120 @@ def ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- batch mode
+def batch_mode(args):
+    """64 independent meshes solved by one nm_batch_potential call (FP32),
+    against the same meshes solved one by one in FP32 and in plain FP64."""
+    import torch
+    from paper_2301_06763_gb300 import build
+    build.build()
+    from paper_2301_06763_gb300 import nm, workloads as wl
+    meshes = wl.config_batch(seed=0)
+    dev = torch.device("cuda", 0)
+    plans32, plans64, r32, r64, phis = [], [], [], [], []
+    cells = 0
+    for w in meshes:
+        rho = w.rho()
+        cells += rho.size
+        plans32.append(nm.Plan(w.levels, w.N, w.dx0, precision="fp32"))
+        plans64.append(nm.Plan(w.levels, w.N, w.dx0, precision="fp64"))
+        r32.append(torch.from_numpy(rho).to(dev, torch.float32))
+        r64.append(torch.from_numpy(rho).to(dev, torch.float64))
+        phis.append(torch.empty(rho.shape, dtype=torch.float64, device=dev))
+    tuned = {}
+    if not args.no_autotune:
+        for p, r, f in zip(plans32, r32, phis):
+            key = (p.levels, p.N)
+            if key not in tuned:
+                tuned[key] = p.autotune(r, f, reps=2)
+            else:
+                p.set_schedule(**tuned[key])
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    l0 = nm.kernel_launches()
+    nm.batch_potential(plans32, r32, phis)
+    per_batch_launches = nm.kernel_launches() - l0
+    ms_batch = timed(lambda: nm.batch_potential(plans32, r32, phis), args.steps)
+    ms_seq32 = timed(lambda: [p.potential(r, f) for p, r, f in zip(plans32, r32, phis)], args.steps)
+    ms_seq64 = timed(lambda: [p.potential(r, f) for p, r, f in zip(plans64, r64, phis)],
+                     max(1, args.steps // 4))
+    line = {"mode": "batch", "metric": "meshes/s, 64-mesh batch (N in {32,64,128}, 2-8 levels)",
+            "unit": "meshes/s", "value": 64 / (ms_batch / 1e3), "ms_per_batch": ms_batch,
+            "fp32_one_by_one_ms": ms_seq32, "fp64_plain_one_by_one_ms": ms_seq64,
+            "speedup_vs_fp64_plain": ms_seq64 / ms_batch, "speedup_vs_fp32_one_by_one": ms_seq32 / ms_batch,
+            "cells": cells, "kernels_per_batch_eager": per_batch_launches,
+            "graph": "batch replayed as one CUDA graph after the first repeat",
+            "shapes": sorted(set((w.levels, w.N) for w in meshes)),
+            "schedules": {"%dx%d" % k: v for k, v in tuned.items()}, "steps": args.steps,
+            "data": "synthetic", "dtype": "f32"}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- serve mode
+def serve_mode(args):
+    """Poisson request streams at several rates through the continuous-batching
+    server: solves/s and p50/p99 latency (arrival to potentials on the host)."""
+    import torch
+    from paper_2301_06763_gb300 import build
+    build.build()
+    from paper_2301_06763_gb300 import nm, workloads as wl
+    from paper_2301_06763_gb300.serve import Request, Server, latency_stats, run_stream
+    # one density per N, sampled for the deepest mesh (10 levels) and sliced:
+    # level m of a mesh is the same set of cells whatever its level count
+    dens = {}
+    rng = np.random.default_rng(0)
+    for N in (32, 64, 128, 256):
+        w = wl.Workload("serve-%d" % N, 10, N, 1.0 / N, wl.random_plummers(rng, 10, N))
+        dens[N] = torch.from_numpy(np.ascontiguousarray(w.rho().astype(np.float32))).pin_memory()
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    results = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        count = int(min(2000, max(20, rate * args.serve_seconds)))
+        arrivals = wl.config_serving(rate, count=count, seed=0)
+        reqs = []
+        for i, (t, w) in enumerate(arrivals):
+            reqs.append(Request(i, w.levels, w.N, w.dx0, dens[w.N][:w.levels], arrival=t,
+                                keep_result=False))
+        srv = Server(budget, slots=4, precision="fp32")
+        # warm the pool: one request per shape, untimed
+        warm = [Request(-1 - i, L, N, 1.0 / N, dens[N][:L], keep_result=False)
+                for i, (L, N) in enumerate(sorted(set((r.levels, r.N) for r in reqs)))]
+        run_stream(srv, warm)
+        srv.completed.clear()
+        elapsed, done = run_stream(srv, reqs)
+        st = latency_stats(done)
+        results.append({"rate": rate, "requests": count, "completed": len(done),
+                        "failed": len(srv.failed), "solves_per_s": len(done) / elapsed,
+                        "batches": srv.batches, "peak_bytes": srv.peak_used, **st})
+        srv.close()
+    print(json.dumps({"mode": "serve", "metric": "served solves/s and latency (arrival -> host potentials)",
+                      "unit": "solves/s", "budget_bytes": budget, "precision": "fp32",
+                      "requests": "N in {32,64,128,256}, 3-10 levels, Poisson arrivals",
+                      "density": "one seeded 1-4 Plummer density per N, sliced to the level count",
+                      "rates": results}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.mode == "batch":
+        batch_mode(args)
+    elif args.mode == "serve":
+        serve_mode(args)
     else:
         ours(args)
 

@@ -89,9 +89,10 @@ typedef struct {
     double dx0;      /* coarsest cell size (> 0); level m has dx0 / 2^m         */
     double G;        /* gravitational constant (Eq. 9); nm_plan uses 1.0        */
     int precision;   /* NM_FP64: all arithmetic in double.  NM_FP32: FFT passes,
-                        spectrum multiply and interpolation in float, Green
-                        spectrum built in double, final per-cell cross-level
-                        sum in double.                                          */
+                        spectrum multiply, interpolation and the sum of the
+                        coarser levels' terms in float; Green spectrum built in
+                        double; the final per-cell addition of that sum to the
+                        level's own potential in double.                        */
     int method;      /* NM_METHOD_ORIGINAL (Eq. 14) or NM_METHOD_DIPOLE_PAIR
                         (Eqs. 15, B.1-B.2)                                       */
     int interp;      /* NM_INTERP_TRILINEAR (the only stencil built)            */
@@ -159,6 +160,11 @@ typedef struct {
     int radix;   /* values per thread = first-pass radix: 16 or 8             */
     int tile;    /* column tile of the strided passes: 0 = 128-byte rows,
                     1 = 256-byte rows                                         */
+    int pipeline;/* z-seam pass: 0 = one tile per CTA; 1 = persistent CTAs fed
+                    by a two-stage TMA (cp.async.bulk.tensor) pipeline        */
+    int fuse;    /* 1 = x and y passes fused per z-slab through a thread-block
+                    cluster (distributed shared memory), 3 launches per level
+                    group instead of 5; needs radix 16; 0 = five passes       */
 } nm_schedule;
 
 /* Read / set the schedule (set reallocates the work buffers when group
@@ -167,7 +173,7 @@ nm_status nm_get_schedule(nm_plan_t plan, nm_schedule* out);
 nm_status nm_set_schedule(nm_plan_t plan, const nm_schedule* sched);
 
 /* Autotuner: times every candidate schedule (group in {1, 2, all}, radix in
- * {16, 8}, tile in {0, 1}) with CUDA events over `reps` solves of the
+ * {16, 8}, tile in {0, 1}, pipeline in {0, 1}, fuse in {0, 1}) with CUDA events over `reps` solves of the
  * caller's rho into phi (phi is overwritten), on `stream`, keeps the fastest
  * on the plan and records it in a process-wide table keyed by (device name,
  * N, levels, precision, method) that later plans of the same key start from.
@@ -185,6 +191,18 @@ nm_status nm_get_options(nm_plan_t plan, nm_options* out);
 
 /* Free the plan and its workspace (synchronises the device first). */
 nm_status nm_destroy(nm_plan_t plan);
+
+/* Device status word: NM_ETIMEOUT once a bounded device-side wait of a
+ * library kernel has run out since the last clear (that kernel stopped early
+ * and the solve's results are invalid), NM_OK otherwise.  Synchronises the
+ * current device; `clear` resets the word. */
+nm_status nm_device_status(int clear);
+
+/* Test hook for failure detection: while `on` is nonzero the TMA-fed z-seam
+ * issues no loads, so its bounded waits run out (after about 0.1 s) and it
+ * raises NM_ETIMEOUT instead of hanging.  Results computed meanwhile are
+ * invalid.  Process-wide. */
+nm_status nm_debug_fault_timeout(int on);
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t nm_kernel_launches(void);

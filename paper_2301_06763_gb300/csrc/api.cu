@@ -190,6 +190,69 @@ static nm_status build_spectrum(Spectrum* s, cudaStream_t stream) {
     return NM_OK;
 }
 
+// ------------------------------------------------------------------ TMA, status
+static std::mutex g_dev_mu;
+static int* g_status[64] = {};
+static int g_sms[64] = {};
+static std::atomic<int> g_fault_timeout{0};
+
+int* device_status_word() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_status[dev]) {
+        int* p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        g_status[dev] = p;
+    }
+    return g_status[dev];
+}
+
+int sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_sms[dev]) {
+        int n = 1;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 1;
+        g_sms[dev] = n;
+    }
+    return g_sms[dev];
+}
+
+bool fault_timeout_on() { return g_fault_timeout.load(std::memory_order_relaxed) != 0; }
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_work_map(CUtensorMap* map, void* work, int P, bool f64, int TX) {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    });
+    if (!fn) return cudaErrorNotSupported;
+    const size_t es = f64 ? 8 : 4;
+    const cuuint64_t dims[3] = {(cuuint64_t)2 * P, (cuuint64_t)P, (cuuint64_t)P / 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)2 * P * es, (cuuint64_t)2 * P * P * es};
+    const cuuint32_t box[3] = {(cuuint32_t)2 * TX, 1u, (cuuint32_t)P / 2};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult r = fn(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, work, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace nm
 
 using namespace nm;
@@ -201,7 +264,7 @@ struct nm_plan_s {
     int N = 0, L = 0, P = 0;
     bool fp32 = false, dipole = false;
     size_t es = 8, cs = 16;           // bytes per real / complex value
-    nm_schedule sched{1, 16, 0};      // level convolutions
+    nm_schedule sched{1, 16, 0, 1, 1};   // level convolutions
     int group_dbl = 1;                // doubled-grid convolutions in flight
     int npairs = 0, npairs_dbl = 0;
     int work_slots = 0;               // work buffers allocated (>= sched.group)
@@ -308,8 +371,9 @@ void tune_load_locked() {
     while (std::fgets(line, sizeof line, f)) {
         char key[300];
         nm_schedule sc;
-        if (std::sscanf(line, " {\"key\": \"%299[^\"]\", \"group\": %d, \"radix\": %d, \"tile\": %d",
-                        key, &sc.group, &sc.radix, &sc.tile) == 4) {
+        if (std::sscanf(line, " {\"key\": \"%299[^\"]\", \"group\": %d, \"radix\": %d, \"tile\": %d, "
+                        "\"pipeline\": %d, \"fuse\": %d", key, &sc.group, &sc.radix, &sc.tile, &sc.pipeline,
+                        &sc.fuse) == 6) {
             bool found = false;
             for (auto& e : g_tune)
                 if (e.key == key) { e.sched = sc; found = true; }
@@ -340,8 +404,10 @@ void tune_store(nm_plan_t p, const nm_schedule& sc) {
     if (path && *path) {
         FILE* f = std::fopen(path, "a");
         if (f) {
-            std::fprintf(f, "{\"key\": \"%s\", \"group\": %d, \"radix\": %d, \"tile\": %d}\n", k.c_str(),
-                         sc.group, sc.radix, sc.tile);
+            std::fprintf(f,
+                         "{\"key\": \"%s\", \"group\": %d, \"radix\": %d, \"tile\": %d, \"pipeline\": %d, "
+                         "\"fuse\": %d}\n",
+                         k.c_str(), sc.group, sc.radix, sc.tile, sc.pipeline, sc.fuse);
             std::fclose(f);
         }
     }
@@ -351,6 +417,9 @@ bool sched_valid(nm_plan_t p, const nm_schedule& sc) {
     if (sc.group < 1 || sc.group > p->npairs) return false;
     if (sc.radix != 8 && sc.radix != 16) return false;
     if (sc.radix == 16 && p->P < 16) return false;
+    if (sc.pipeline != 0 && sc.pipeline != 1) return false;
+    if (sc.fuse != 0 && sc.fuse != 1) return false;
+    if (sc.fuse && sc.radix != 16) return false;
     return sc.tile == 0 || sc.tile == 1;
 }
 
@@ -466,6 +535,8 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     p->sched.group = default_group(work_buf_bytes(p), p->npairs);
     p->sched.radix = p->P >= 16 ? 16 : 8;
     p->sched.tile = 0;
+    p->sched.pipeline = 0;
+    p->sched.fuse = 0;
     nm_schedule tuned;
     if (tune_lookup(p, &tuned) && sched_valid(p, tuned)) p->sched = tuned;
     const size_t buf_dbl = (2 * N) * (4 * N) * (4 * N) * p->cs;
@@ -612,15 +683,16 @@ template <> const cpx<float>* tw_of<float>(const Twiddle* t) { return t->d32; }
 template <> const cpx<double>* tw_of<double>(const Twiddle* t) { return t->d64; }
 
 template <typename T>
-cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, bool dbl, int radix, int tile,
+cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, bool dbl, const nm_schedule& sc,
                      const T* spec, const cpx<T>* tw, cudaStream_t s) {
-    const bool e16 = dbl || (radix == 16 && P >= 16);
+    const bool e16 = dbl || (sc.radix == 16 && P >= 16);
+    const int flags = (sc.tile ? CONV_WIDE : 0) | (sc.pipeline ? CONV_TMA : 0) | (sc.fuse ? CONV_FUSED : 0);
     if constexpr (sizeof(T) == 4) {
-        return e16 ? run_conv_f32_e16(pairs, n, P, dbl, tile != 0, spec, tw, s)
-                   : run_conv_f32_e8(pairs, n, P, dbl, tile != 0, spec, tw, s);
+        return e16 ? run_conv_f32_e16(pairs, n, P, dbl, flags, spec, tw, s)
+                   : run_conv_f32_e8(pairs, n, P, dbl, flags, spec, tw, s);
     } else {
-        return e16 ? run_conv_f64_e16(pairs, n, P, dbl, tile != 0, spec, tw, s)
-                   : run_conv_f64_e8(pairs, n, P, dbl, tile != 0, spec, tw, s);
+        return e16 ? run_conv_f64_e16(pairs, n, P, dbl, flags, spec, tw, s)
+                   : run_conv_f64_e8(pairs, n, P, dbl, flags, spec, tw, s);
     }
 }
 
@@ -700,7 +772,8 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
         }
         for (int r = 0; r < rounds; ++r) {
             struct Bucket {
-                int P, radix, tile;
+                int P;
+                nm_schedule sc;
                 const T* spec;
                 const cpx<T>* tw;
                 std::vector<PairDesc<T>> pairs;
@@ -710,8 +783,7 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
                 nm_plan_t p = items[i].p;
                 const int g = dbl ? p->group_dbl : p->sched.group;
                 const int P = dbl ? 2 * p->P : p->P;
-                const int radix = dbl ? 16 : p->sched.radix;
-                const int tile = dbl ? 0 : p->sched.tile;
+                const nm_schedule sc = dbl ? nm_schedule{1, 16, 0, 0, 0} : p->sched;
                 const size_t buf = (size_t)(P / 2) * P * P;
                 cpx<T>* work = (cpx<T>*)(dbl ? p->dbl_work : p->work);
                 for (int q = r * g; q < (r + 1) * g && q < (int)pl[i].size(); ++q) {
@@ -719,9 +791,11 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
                     d.work = work + (size_t)(q - r * g) * buf;
                     Bucket* b = nullptr;
                     for (auto& bb : buckets)
-                        if (bb.P == P && bb.radix == radix && bb.tile == tile) b = &bb;
+                        if (bb.P == P && bb.sc.radix == sc.radix && bb.sc.tile == sc.tile &&
+                            bb.sc.pipeline == sc.pipeline && bb.sc.fuse == sc.fuse)
+                            b = &bb;
                     if (!b) {
-                        buckets.push_back({P, radix, tile, spec_of<T>(dbl ? p->spec_dbl : p->spec),
+                        buckets.push_back({P, sc, spec_of<T>(dbl ? p->spec_dbl : p->spec),
                                            tw_of<T>(dbl ? p->tw_dbl : p->tw), {}});
                         b = &buckets.back();
                     }
@@ -729,8 +803,8 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
                 }
             }
             for (auto& b : buckets) {
-                cudaError_t e = run_conv<T>(b.pairs.data(), (int)b.pairs.size(), b.P, dbl, b.radix,
-                                            b.tile, b.spec, b.tw, s);
+                cudaError_t e = run_conv<T>(b.pairs.data(), (int)b.pairs.size(), b.P, dbl, b.sc, b.spec,
+                                            b.tw, s);
                 if (e != cudaSuccess) return cuda_fail(e, dbl ? "doubled-grid convolution" : "level convolution");
             }
         }
@@ -825,8 +899,9 @@ nm_status nm_batch_potential(int n, const nm_plan_t* plans, const void* const* r
         key.push_back(plans[i]);
         key.push_back(rho[i]);
         key.push_back(phi[i]);
-        key.push_back((const void*)(uintptr_t)((plans[i]->sched.group << 8) | (plans[i]->sched.radix << 1) |
-                                               plans[i]->sched.tile));
+        key.push_back((const void*)(uintptr_t)((plans[i]->sched.group << 12) | (plans[i]->sched.radix << 3) |
+                                               (plans[i]->sched.fuse << 2) | (plans[i]->sched.tile << 1) |
+                                               plans[i]->sched.pipeline));
     }
     if (n == 0) return NM_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -834,7 +909,7 @@ nm_status nm_batch_potential(int n, const nm_plan_t* plans, const void* const* r
         nm_status st = ensure_green(it.p, s);
         if (st != NM_OK) return st;
     }
-    if (g_prof_on.load() || env_int("NM_NO_GRAPHS", 0)) return enqueue_all(items, s);
+    if (g_prof_on.load() || fault_timeout_on() || env_int("NM_NO_GRAPHS", 0)) return enqueue_all(items, s);
     // repeated batch: replay its graph; first repeat: capture it
     cudaGraphExec_t exec = nullptr;
     bool seen = false;
@@ -891,7 +966,8 @@ nm_status nm_get_schedule(nm_plan_t p, nm_schedule* out) {
 nm_status nm_set_schedule(nm_plan_t p, const nm_schedule* sc) {
     if (!p || !sc) return fail(NM_EINVAL, "nm_set_schedule: null argument");
     if (!sched_valid(p, *sc))
-        return fail(NM_EINVAL, "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile 0 or 1",
+        return fail(NM_EINVAL,
+                    "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile and pipeline 0 or 1",
                     p->npairs);
     nm_status st = ensure_work_slots(p, sc->group);
     if (st != NM_OK) return st;
@@ -909,14 +985,18 @@ nm_status nm_autotune(nm_plan_t p, const void* rho, double* phi, int reps, void*
     std::vector<nm_schedule> cands;
     for (int g : groups)
         for (int radix : {16, 8})
-            for (int tile : {0, 1}) {
-                nm_schedule c{g, radix, tile};
-                if (!sched_valid(p, c)) continue;
-                bool dup = false;
-                for (auto& o : cands)
-                    if (o.group == c.group && o.radix == c.radix && o.tile == c.tile) dup = true;
-                if (!dup) cands.push_back(c);
-            }
+            for (int tile : {0, 1})
+                for (int pipe : {1, 0})
+                    for (int fuse : {1, 0}) {
+                        nm_schedule c{g, radix, tile, pipe, fuse};
+                        if (!sched_valid(p, c)) continue;
+                        bool dup = false;
+                        for (auto& o : cands)
+                            if (o.group == c.group && o.radix == c.radix && o.tile == c.tile &&
+                                o.pipeline == c.pipeline && o.fuse == c.fuse)
+                                dup = true;
+                        if (!dup) cands.push_back(c);
+                    }
     nm_status st = ensure_work_slots(p, p->npairs);
     if (st != NM_OK) return st;
     graphs_drop_plan(p);
@@ -987,6 +1067,22 @@ nm_status nm_destroy(nm_plan_t p) {
 }
 
 uint64_t nm_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+nm_status nm_device_status(int clear) {
+    int* w = device_status_word();
+    if (!w) return fail(NM_ECUDA, "nm_device_status: no status word");
+    NM_CUDA(cudaDeviceSynchronize(), "nm_device_status sync");
+    int v = 0;
+    NM_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost), "nm_device_status read");
+    if (clear) NM_CUDA(cudaMemset(w, 0, sizeof(int)), "nm_device_status clear");
+    if (v == NM_ETIMEOUT) return fail(NM_ETIMEOUT, "a bounded device-side wait ran out");
+    return NM_OK;
+}
+
+nm_status nm_debug_fault_timeout(int on) {
+    g_fault_timeout.store(on ? 1 : 0);
+    return NM_OK;
+}
 
 nm_status nm_profile_enable(int on) {
     if (on) prof_clear();

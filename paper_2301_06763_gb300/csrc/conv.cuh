@@ -156,8 +156,11 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
 }
 
 // ---------------------------------------------------------------- pass 3
+// At least 1024 resident threads per SM (4 CTAs of 256): the seam holds two
+// transforms' worth of live values, and more warps hide its load latency.
 template <typename T, int P, int E, int TX, bool DBL>
-__global__ void __launch_bounds__(TX * P / E) k_zseam(const __grid_constant__ ConvArgs<T> a) {
+__global__ void __launch_bounds__(TX * P / E, (1024 / (TX * P / E)) > 0 ? 1024 / (TX * P / E) : 1)
+    k_zseam(const __grid_constant__ ConvArgs<T> a) {
     using G = Geo<P, E, DBL>;
     constexpr int H = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];

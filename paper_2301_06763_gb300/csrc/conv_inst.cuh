@@ -3,7 +3,9 @@
 // the conv_*.cu translation units so the variants compile in parallel.
 #pragma once
 #include <cstdio>
+#include <mutex>
 
+#include "fused.cuh"
 #include "internal.h"
 
 namespace nm {
@@ -13,9 +15,94 @@ static cudaError_t prep_kernel(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Persistent TMA-fed z-seam over all pairs of the launch (see tma.cuh).
+template <typename T, int P, int E, int TX>
+static cudaError_t zseam_tma(const ConvArgs<T>& a, int np, cudaStream_t s) {
+    constexpr int NT = TX * P / E;
+    const size_t c = sizeof(cpx<T>);
+    const size_t smem = 2 * (size_t)P * TX * c + (size_t)P * c + 2 * sizeof(uint64_t);
+    static int occ = -1;   // resident CTAs per SM, computed once per kernel
+    static const cudaError_t prepared = [&]() {
+        cudaError_t e = prep_kernel(k_zseam_tma<T, P, E, TX>, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zseam_tma<T, P, E, TX>, NT, smem);
+        return e;
+    }();
+    if (prepared != cudaSuccess) return prepared;
+    static TmaArgs<T> ta;   // host staging of the (large) parameter block
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    ta.spec = a.spec;
+    ta.tw = a.tw;
+    ta.npairs = np;
+    ta.fault_skip_load = fault_timeout_on() ? 1 : 0;
+    ta.timeout = ta.fault_skip_load ? 200000000LL : 4000000000LL;
+    ta.status = device_status_word();
+    for (int i = 0; i < np; ++i) {
+        cudaError_t e = encode_work_map(&ta.map[i], a.pair[i].work, P, sizeof(T) == 8, TX);
+        if (e != cudaSuccess) return e;
+    }
+    const int total = np * P * (P / TX);
+    int grid = (occ > 0 ? occ : 1) * sm_count();
+    if (grid > total) grid = total;
+    k_zseam_tma<T, P, E, TX><<<grid, NT, smem, s>>>(ta);
+    return cudaSuccess;
+}
+
+// x and y passes fused per slab through a cluster (see fused.cuh); `fwd`
+// selects the forward (x then y) or inverse (y then x) kernel.
+template <typename T, int P>
+static cudaError_t fused_pass(const ConvArgs<T>& a, int np, bool fwd, cudaStream_t s) {
+    using F = FusedShape<T, P>;
+    static const cudaError_t prepared = [&]() {
+        cudaError_t e = prep_kernel(k_xyfwd<T, T, P>, F::SMEM);
+        if (e == cudaSuccess) e = prep_kernel(k_yxinv<T, P>, F::SMEM_INV);
+        return e;
+    }();
+    if (prepared != cudaSuccess) return prepared;
+    const dim3 grid(F::N * F::C, np);
+    if (fwd) k_xyfwd<T, T, P><<<grid, F::NT, F::SMEM, s>>>(a);
+    else k_yxinv<T, P><<<grid, F::NT, F::SMEM_INV, s>>>(a);
+    return cudaGetLastError();
+}
+
 // W = requested column-tile width of the strided passes.
 template <typename T, int P, int E, int W, bool DBL>
-static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
+static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStream_t s) {
+    const bool tma = (flags & CONV_TMA) != 0;
+    if constexpr (!DBL && E == 16 && FusedShape<T, P>::OK) {
+        if (flags & CONV_FUSED) {
+            constexpr int TX = Tile<P, E, W>::TX;
+            const char* tag = sizeof(T) == 4 ? "f32" : "f64";
+            char nm_[48];
+            cudaError_t e;
+            {
+                snprintf(nm_, sizeof nm_, "xyfwd_%s_P%d", tag, P);
+                ProfScope ps(nm_, np, s);
+                if ((e = fused_pass<T, P>(a, np, true, s)) != cudaSuccess) return e;
+            }
+            {
+                snprintf(nm_, sizeof nm_, "zseam_%s_P%d", tag, P);
+                ProfScope ps(nm_, np, s);
+                if (tma) {
+                    if ((e = zseam_tma<T, P, E, TX>(a, np, s)) != cudaSuccess) return e;
+                } else {
+                    constexpr int NT = TX * P / E;
+                    const size_t sm_yz = (size_t)P * sizeof(cpx<T>) + (size_t)TX * P * sizeof(cpx<T>);
+                    static const cudaError_t prep = prep_kernel(k_zseam<T, P, E, TX, false>, sm_yz);
+                    if (prep != cudaSuccess) return prep;
+                    k_zseam<T, P, E, TX, false><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+                }
+            }
+            {
+                snprintf(nm_, sizeof nm_, "yxinv_%s_P%d", tag, P);
+                ProfScope ps(nm_, np, s);
+                if ((e = fused_pass<T, P>(a, np, false, s)) != cudaSuccess) return e;
+            }
+            count_launches(3);
+            return cudaGetLastError();
+        }
+    }
     using Gm = Geo<P, E, DBL>;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
@@ -52,7 +139,16 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, cudaStream_t s) {
     {
         snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_zseam<T, P, E, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+        if constexpr (!DBL) {
+            if (tma) {
+                cudaError_t e = zseam_tma<T, P, E, TX>(a, np, s);
+                if (e != cudaSuccess) return e;
+            } else {
+                k_zseam<T, P, E, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+            }
+        } else {
+            k_zseam<T, P, E, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+        }
     }
     {
         snprintf(nm_, sizeof nm_, "yinv%s_%s_P%d", geo, tag, P);
@@ -76,39 +172,39 @@ template <typename T> struct Widths {
 };
 
 template <typename T, int P, int E, bool DBL>
-static cudaError_t conv_width(const ConvArgs<T>& a, int np, bool wide, cudaStream_t s) {
-    if (wide) return conv_passes<T, P, E, Widths<T>::WIDE, DBL>(a, np, s);
-    return conv_passes<T, P, E, Widths<T>::NARROW, DBL>(a, np, s);
+static cudaError_t conv_width(const ConvArgs<T>& a, int np, int flags, cudaStream_t s) {
+    if (flags & CONV_WIDE) return conv_passes<T, P, E, Widths<T>::WIDE, DBL>(a, np, flags, s);
+    return conv_passes<T, P, E, Widths<T>::NARROW, DBL>(a, np, flags, s);
 }
 
 // The doubled-grid geometry is instantiated only with the default schedule
 // (E = 16, narrow tiles) to bound compile time.
 template <typename T, int E>
-static cudaError_t conv_dispatch(const ConvArgs<T>& a, int np, int P, bool dbl, bool wide,
+static cudaError_t conv_dispatch(const ConvArgs<T>& a, int np, int P, bool dbl, int flags,
                                  cudaStream_t s) {
     if (dbl) {
         if constexpr (E == 16) {
             switch (P) {
-                case 16: return conv_passes<T, 16, 16, Widths<T>::NARROW, true>(a, np, s);
-                case 32: return conv_passes<T, 32, 16, Widths<T>::NARROW, true>(a, np, s);
-                case 64: return conv_passes<T, 64, 16, Widths<T>::NARROW, true>(a, np, s);
-                case 128: return conv_passes<T, 128, 16, Widths<T>::NARROW, true>(a, np, s);
-                case 256: return conv_passes<T, 256, 16, Widths<T>::NARROW, true>(a, np, s);
-                case 512: return conv_passes<T, 512, 16, Widths<T>::NARROW, true>(a, np, s);
-                case 1024: return conv_passes<T, 1024, 16, Widths<T>::NARROW, true>(a, np, s);
+                case 16: return conv_passes<T, 16, 16, Widths<T>::NARROW, true>(a, np, 0, s);
+                case 32: return conv_passes<T, 32, 16, Widths<T>::NARROW, true>(a, np, 0, s);
+                case 64: return conv_passes<T, 64, 16, Widths<T>::NARROW, true>(a, np, 0, s);
+                case 128: return conv_passes<T, 128, 16, Widths<T>::NARROW, true>(a, np, 0, s);
+                case 256: return conv_passes<T, 256, 16, Widths<T>::NARROW, true>(a, np, 0, s);
+                case 512: return conv_passes<T, 512, 16, Widths<T>::NARROW, true>(a, np, 0, s);
+                case 1024: return conv_passes<T, 1024, 16, Widths<T>::NARROW, true>(a, np, 0, s);
                 default: break;
             }
         }
         return cudaErrorInvalidValue;
     }
     switch (P) {
-        case 8: if constexpr (E == 8) return conv_width<T, 8, 8, false>(a, np, wide, s); break;
-        case 16: return conv_width<T, 16, E, false>(a, np, wide, s);
-        case 32: return conv_width<T, 32, E, false>(a, np, wide, s);
-        case 64: return conv_width<T, 64, E, false>(a, np, wide, s);
-        case 128: return conv_width<T, 128, E, false>(a, np, wide, s);
-        case 256: return conv_width<T, 256, E, false>(a, np, wide, s);
-        case 512: return conv_width<T, 512, E, false>(a, np, wide, s);
+        case 8: if constexpr (E == 8) return conv_width<T, 8, 8, false>(a, np, flags, s); break;
+        case 16: return conv_width<T, 16, E, false>(a, np, flags, s);
+        case 32: return conv_width<T, 32, E, false>(a, np, flags, s);
+        case 64: return conv_width<T, 64, E, false>(a, np, flags, s);
+        case 128: return conv_width<T, 128, E, false>(a, np, flags, s);
+        case 256: return conv_width<T, 256, E, false>(a, np, flags, s);
+        case 512: return conv_width<T, 512, E, false>(a, np, flags, s);
         default: break;
     }
     return cudaErrorInvalidValue;
@@ -116,14 +212,14 @@ static cudaError_t conv_dispatch(const ConvArgs<T>& a, int np, int P, bool dbl, 
 
 template <typename T, int E>
 static cudaError_t run_conv_variant(const PairDesc<T>* pairs, int npairs, int P, bool dbl,
-                                    bool wide, const T* spec, const cpx<T>* tw, cudaStream_t s) {
+                                    int flags, const T* spec, const cpx<T>* tw, cudaStream_t s) {
     ConvArgs<T> a;
     a.spec = spec;
     a.tw = tw;
     for (int i0 = 0; i0 < npairs; i0 += kMaxPairs) {
         const int np = npairs - i0 < kMaxPairs ? npairs - i0 : kMaxPairs;
         for (int i = 0; i < np; ++i) a.pair[i] = pairs[i0 + i];
-        cudaError_t e = conv_dispatch<T, E>(a, np, P, dbl, wide, s);
+        cudaError_t e = conv_dispatch<T, E>(a, np, P, dbl, flags, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

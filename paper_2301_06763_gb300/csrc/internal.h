@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "conv.cuh"
+#include "tma.cuh"
 
 namespace nm {
 
@@ -21,17 +22,30 @@ struct ProfScope {
 };
 
 // Five-pass convolution of `npairs` packed pairs of FFT size P (see conv.cuh),
-// one entry point per (precision, values per thread); `wide` selects the wider
-// column tile.  DBL selects the doubled-fine-grid geometry (16 values, narrow
-// tiles only).  Returns the first launch error.
-cudaError_t run_conv_f32_e16(const PairDesc<float>* pairs, int npairs, int P, bool dbl, bool wide,
+// one entry point per (precision, values per thread).  `flags`: CONV_WIDE
+// selects the wider column tile, CONV_TMA the persistent TMA-fed z-seam,
+// CONV_FUSED the cluster-fused x/y passes (level grids only; 16 values per
+// thread; sizes whose slab does not fit a cluster keep the five passes).  DBL selects the doubled-fine-grid geometry (16 values,
+// narrow tiles only).  Returns the first launch error.
+enum { CONV_WIDE = 1, CONV_TMA = 2, CONV_FUSED = 4 };
+cudaError_t run_conv_f32_e16(const PairDesc<float>* pairs, int npairs, int P, bool dbl, int flags,
                              const float* spec, const cpx<float>* tw, cudaStream_t s);
-cudaError_t run_conv_f32_e8(const PairDesc<float>* pairs, int npairs, int P, bool dbl, bool wide,
+cudaError_t run_conv_f32_e8(const PairDesc<float>* pairs, int npairs, int P, bool dbl, int flags,
                             const float* spec, const cpx<float>* tw, cudaStream_t s);
-cudaError_t run_conv_f64_e16(const PairDesc<double>* pairs, int npairs, int P, bool dbl, bool wide,
+cudaError_t run_conv_f64_e16(const PairDesc<double>* pairs, int npairs, int P, bool dbl, int flags,
                              const double* spec, const cpx<double>* tw, cudaStream_t s);
-cudaError_t run_conv_f64_e8(const PairDesc<double>* pairs, int npairs, int P, bool dbl, bool wide,
+cudaError_t run_conv_f64_e8(const PairDesc<double>* pairs, int npairs, int P, bool dbl, int flags,
                             const double* spec, const cpx<double>* tw, cudaStream_t s);
+
+// TMA descriptor of one work buffer ([P/2][P][P] complex, seen as
+// [P/2][P][2P] reals) with a box of TX columns x 1 row x P/2 slabs.
+cudaError_t encode_work_map(CUtensorMap* map, void* work, int P, bool f64, int TX);
+// The library's device status word on the current device (0 = fine).
+int* device_status_word();
+// Test hook: while set, TMA-fed kernels issue no loads so their bounded
+// waits run out (see nm_debug_fault_timeout).
+bool fault_timeout_on();
+int sm_count();
 
 // Unit-cell kernel spectrum octant (N+1)^3 in double (Eqs. 10, 13, Fig. 4);
 // `scratch` holds 2 (N+1)^3 doubles, `ctab` the P = 2N cosines cos(2 pi t/P).

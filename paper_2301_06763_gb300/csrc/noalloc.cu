@@ -125,14 +125,14 @@ cudaError_t solve_static(const nm_options& o, char* base, const Layout& lay, con
             d.dst[1] = DstField{nullptr, DST_NONE};
         }
         if (P >= 16)
-            e = f32 ? run_conv_f32_e16((const PairDesc<float>*)(const void*)&d, 1, P, false, false,
+            e = f32 ? run_conv_f32_e16((const PairDesc<float>*)(const void*)&d, 1, P, false, 0,
                                        (const float*)(const void*)spec, (const cpx<float>*)(const void*)tw, s)
-                    : run_conv_f64_e16((const PairDesc<double>*)(const void*)&d, 1, P, false, false,
+                    : run_conv_f64_e16((const PairDesc<double>*)(const void*)&d, 1, P, false, 0,
                                        (const double*)(const void*)spec, (const cpx<double>*)(const void*)tw, s);
         else
-            e = f32 ? run_conv_f32_e8((const PairDesc<float>*)(const void*)&d, 1, P, false, false,
+            e = f32 ? run_conv_f32_e8((const PairDesc<float>*)(const void*)&d, 1, P, false, 0,
                                       (const float*)(const void*)spec, (const cpx<float>*)(const void*)tw, s)
-                    : run_conv_f64_e8((const PairDesc<double>*)(const void*)&d, 1, P, false, false,
+                    : run_conv_f64_e8((const PairDesc<double>*)(const void*)&d, 1, P, false, 0,
                                       (const double*)(const void*)spec, (const cpx<double>*)(const void*)tw, s);
         if (e != cudaSuccess) return e;
     }

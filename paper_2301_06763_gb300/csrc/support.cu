@@ -130,8 +130,11 @@ cudaError_t run_to_float(const double* in, float* out, size_t n, cudaStream_t s)
 //   u = N/2 - N/(2r) + (i + 1/2)/r - 1/2,  r = 2^(n-k),
 // i.e. 2r u = (N - 1)(r - 1) + 2i, so the stencil corner and weight follow in
 // integer arithmetic (shifts: N and r are powers of two) and the weights are
-// exact.  Each interpolated term is formed in T; the per-cell sum over levels
-// is accumulated in double.
+// exact.  The coarser levels' interpolated terms (and the reduced doubled
+// grid) are summed in T; the final per-cell addition of that cross-level sum to
+// the level's own potential is done in double (FP64 mode: everything in
+// double).  GB300's FP64 pipe runs at 1/69 of its FP32 rate, so the FP32 path
+// spends one double addition per cell.
 template <typename T>
 __device__ __forceinline__ void axis_stencil(int N, int lgr, int i, int& i0, T& t) {
     const int num = (N - 1) * ((1 << lgr) - 1) + 2 * i;
@@ -195,9 +198,7 @@ __global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
                   z = (int)(cell >> (2 * lgN));
         T b[4];
         Vec4<T>::load(a.base[n] + cell, b);
-        double acc[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] = widen(b[c]);
+        T acc[4] = {T(0), T(0), T(0), T(0)};   // cross-level sum
         if (a.dbl[n]) {
             const int E = 2 * N;
             const T* d = a.dbl[n];
@@ -211,7 +212,7 @@ __global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
                         const T* row = d + ((size_t)(2 * z + dz) * E + (2 * y + dy)) * E + 2 * (x0 + c);
                         s += row[0] + row[1];
                     }
-                acc[c] += widen(s * T(0.125));
+                acc[c] += s * T(0.125);
             }
         }
         for (int k = 0; k < n; ++k) {
@@ -235,12 +236,12 @@ __global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
                 const T c11 = src[sz + sy] + tx * (src[sz + sy + 1] - src[sz + sy]);
                 const T c0 = c00 + ty * (c01 - c00);
                 const T c1 = c10 + ty * (c11 - c10);
-                acc[c] += widen(c0 + tz * (c1 - c0));
+                acc[c] += c0 + tz * (c1 - c0);
             }
         }
         double2* out = reinterpret_cast<double2*>(a.phi + idx);
-        out[0] = make_double2(acc[0], acc[1]);
-        out[1] = make_double2(acc[2], acc[3]);
+        out[0] = make_double2(widen(b[0]) + widen(acc[0]), widen(b[1]) + widen(acc[1]));
+        out[1] = make_double2(widen(b[2]) + widen(acc[2]), widen(b[3]) + widen(acc[3]));
     }
 }
 

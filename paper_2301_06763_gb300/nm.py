@@ -30,10 +30,12 @@ class Options(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("group", ctypes.c_int), ("radix", ctypes.c_int), ("tile", ctypes.c_int)]
+    _fields_ = [("group", ctypes.c_int), ("radix", ctypes.c_int), ("tile", ctypes.c_int),
+                ("pipeline", ctypes.c_int), ("fuse", ctypes.c_int)]
 
     def as_dict(self):
-        return {"group": self.group, "radix": self.radix, "tile": self.tile}
+        return {"group": self.group, "radix": self.radix, "tile": self.tile, "pipeline": self.pipeline,
+                "fuse": self.fuse}
 
 
 class KernelStat(ctypes.Structure):
@@ -81,6 +83,8 @@ def lib():
             "nm_autotune": (st, [P, P, P, ctypes.c_int, P]),
             "nm_potential_noalloc": (st, [ctypes.POINTER(Options), P, P, P]),
             "nm_kernel_launches": (ctypes.c_uint64, []),
+            "nm_device_status": (st, [ctypes.c_int]),
+            "nm_debug_fault_timeout": (st, [ctypes.c_int]),
             "nm_profile_enable": (st, [ctypes.c_int]),
             "nm_profile_read": (st, [ctypes.POINTER(KernelStat), ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int)]),
@@ -128,6 +132,16 @@ def footprint_bytes(levels, N, dx0=1.0, G=1.0, precision="fp64", method="origina
     _check(lib().nm_footprint_bytes(ctypes.byref(make_options(levels, N, dx0, G, precision, method)),
                                     ctypes.byref(v)))
     return int(v.value)
+
+
+def device_status(clear=True):
+    """NM_OK, or NM_ETIMEOUT if a bounded device wait ran out (synchronises)."""
+    return int(lib().nm_device_status(1 if clear else 0))
+
+
+def debug_fault_timeout(on):
+    """Test hook: make the TMA-fed kernels' waits run out (see nm.h)."""
+    _check(lib().nm_debug_fault_timeout(1 if on else 0))
 
 
 def profile_enable(on=True):
@@ -218,8 +232,8 @@ class Plan:
         _check(lib().nm_get_schedule(self.handle, ctypes.byref(sc)))
         return sc.as_dict()
 
-    def set_schedule(self, group, radix, tile):
-        sc = Schedule(int(group), int(radix), int(tile))
+    def set_schedule(self, group, radix, tile, pipeline=0, fuse=0):
+        sc = Schedule(int(group), int(radix), int(tile), int(pipeline), int(fuse))
         _check(lib().nm_set_schedule(self.handle, ctypes.byref(sc)))
 
     def autotune(self, rho, phi=None, reps=3, stream=None):

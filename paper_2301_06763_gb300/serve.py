@@ -32,7 +32,7 @@ class Request:
     def __init__(self, rid, levels, N, dx0, rho, arrival=0.0, G=1.0, keep_result=True):
         self.rid = rid
         self.levels, self.N, self.dx0, self.G = int(levels), int(N), float(dx0), float(G)
-        self.rho = rho                  # host array (levels, N, N, N), float32/float64
+        self.rho = rho                  # host (levels, N, N, N): numpy array or (pinned) CPU tensor
         self.arrival = float(arrival)   # wall-clock seconds (perf_counter) of arrival
         self.keep_result = keep_result
         self.admitted = None
@@ -179,10 +179,12 @@ class Server:
         with torch.cuda.stream(s):
             for r in batch:
                 shape = (r.levels, r.N, r.N, r.N)
-                r._rho_pin = torch.from_numpy(np.ascontiguousarray(r.rho, dtype=np.float32 if
-                                              self.precision == "fp32" else np.float64))
-                if not r._rho_pin.is_pinned():
-                    r._rho_pin = r._rho_pin.pin_memory()
+                if isinstance(r.rho, torch.Tensor) and r.rho.is_pinned() and r.rho.dtype == self._dtype():
+                    r._rho_pin = r.rho                  # caller-pinned: no host copy
+                else:
+                    arr = r.rho.numpy() if isinstance(r.rho, torch.Tensor) else r.rho
+                    r._rho_pin = torch.from_numpy(np.ascontiguousarray(
+                        arr, dtype=np.float32 if self.precision == "fp32" else np.float64)).pin_memory()
                 r._rho_dev = torch.empty(shape, dtype=self._dtype(), device=self.device)
                 r._phi_dev = torch.empty(shape, dtype=torch.float64, device=self.device)
                 r._rho_dev.copy_(r._rho_pin, non_blocking=True)

@@ -79,13 +79,18 @@ def test_every_schedule_matches_the_oracle(precision):
         for group in (1, 2, 4):
             for radix in (16, 8):
                 for tile in (0, 1):
-                    p.set_schedule(group, radix, tile)
-                    assert p.schedule() == {"group": group, "radix": radix, "tile": tile}
-                    assert rel_max(p.potential(r).cpu().numpy(), ref) <= tol
+                    for pipe in (0, 1):
+                        for fuse in ((0, 1) if radix == 16 else (0,)):
+                            p.set_schedule(group, radix, tile, pipe, fuse)
+                            assert p.schedule() == {"group": group, "radix": radix, "tile": tile,
+                                                    "pipeline": pipe, "fuse": fuse}
+                            assert rel_max(p.potential(r).cpu().numpy(), ref) <= tol
         with pytest.raises(m.NMError):
             p.set_schedule(5, 16, 0)
         with pytest.raises(m.NMError):
             p.set_schedule(1, 4, 0)
+        with pytest.raises(m.NMError):
+            p.set_schedule(1, 8, 0, 0, 1)      # fused passes need radix 16
 
 
 def test_autotune_picks_a_valid_schedule_and_caches_it(tmp_path, monkeypatch):
@@ -96,6 +101,7 @@ def test_autotune_picks_a_valid_schedule_and_caches_it(tmp_path, monkeypatch):
     with m.Plan(L, N, 1.0 / N, precision="fp32") as p:
         sc = p.autotune(rho, reps=2)
         assert 1 <= sc["group"] <= L and sc["radix"] in (8, 16) and sc["tile"] in (0, 1)
+        assert sc["pipeline"] in (0, 1) and sc["fuse"] in (0, 1)
         ref = p.potential(rho).cpu().numpy()
     # a later plan of the same shape starts from the tuned schedule
     with m.Plan(L, N, 1.0 / N, precision="fp32") as q:
