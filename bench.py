@@ -143,7 +143,7 @@ def source_hash():
 
 
 def ncu_traffic(kernel_name):
-    """Per-launch DRAM bytes of `kernel_name` from the committed ncu summary, or
+    """DRAM bytes per pair of `kernel_name` from the committed ncu summary, or
     None when no summary exists or the kernel sources changed since."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     if not os.path.exists(path):
@@ -152,7 +152,7 @@ def ncu_traffic(kernel_name):
     m = re.search(r"source hash:\s*`?([0-9a-f]+)", text)
     if not m or m.group(1) != source_hash():
         return None
-    m = re.search(r"^\|\s*%s\s*\|[^|]*\|\s*([0-9.e+]+)\s*\|" % re.escape(kernel_name), text, re.M)
+    m = re.search(r"^\|\s*%s\s*\|[^|]*\|[^|]*\|\s*([0-9.e+]+)\s*\|" % re.escape(kernel_name), text, re.M)
     return float(m.group(1)) if m else None
 
 
@@ -338,7 +338,8 @@ def ours(args):
     if per_unit is not None:
         bytes_launch = per_unit * du / dl
         achieved = bytes_launch / (dms / dl * 1e-3) / 1e9
-        traffic = ncu_traffic(dname)
+        per_pair = ncu_traffic(dname)
+        traffic = per_pair * du / dl if per_pair is not None else None
         roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,

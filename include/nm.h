@@ -119,7 +119,10 @@ nm_status nm_green(nm_plan_t plan, void* stream);
 
 /* The potential of every cell of every level (see the header comment) from
  * densities `rho` (device, L*N^3, double or float by precision) into `phi`
- * (device, L*N^3 double).  Asynchronous on `stream`.  `rho` is read only. */
+ * (device, L*N^3 double).  Asynchronous on `stream`.  `rho` is read only.
+ * A repeated call with the same (plan, rho, phi) replays a CUDA graph of the
+ * solve captured on the first repeat (as nm_batch_potential does); inside a
+ * caller's own stream capture the kernels are simply recorded. */
 nm_status nm_potential(nm_plan_t plan, const void* rho, double* phi, void* stream);
 
 /* Same result from HOST buffers: copies rho to the device, solves, copies phi

@@ -308,13 +308,14 @@ void plan_free_buffers(nm_plan_t p) {
     p->h_phi = nullptr;
 }
 
-// Pairs in flight per launch: all of them while one pair's work buffer is
-// small, one at a time once a buffer is large enough that keeping it resident
-// in L2 between passes matters more than filling the GPU with several.
+// Pairs in flight per launch: as many as fit in 1 GiB of work buffers.  On
+// GB300 one launch over all levels beats per-level launches that would keep a
+// level's intermediate resident in L2 (measured for 6 x 128^3: 0.67 vs 0.78
+// ms per FP32 solve), so only memory bounds the group.
 int default_group(size_t buf_bytes, int npairs) {
     int g = env_int("NM_GROUP", 0);
     if (g <= 0) {
-        const size_t budget = (size_t)64 << 20;
+        const size_t budget = (size_t)1 << 30;
         g = buf_bytes >= budget ? 1 : (int)(budget / buf_bytes);
     }
     if (g > npairs) g = npairs;
@@ -428,10 +429,11 @@ struct BatchGraph {
     std::vector<const void*> key;
     cudaGraphExec_t exec = nullptr;
     bool captured = false;
+    uint64_t kernels = 0;   // kernel nodes in the graph (counted again per replay)
 };
 std::mutex g_graph_mu;
 std::vector<BatchGraph> g_graphs;   // most recent last
-constexpr size_t kMaxGraphs = 8;
+constexpr size_t kMaxGraphs = 32;
 
 void graphs_drop_plan(nm_plan_t p) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
@@ -854,6 +856,83 @@ nm_status time_solves(nm_plan_t p, const void* rho, double* phi, int reps, cudaS
     return NM_OK;
 }
 
+// Issue a set of solves: a set seen before is replayed from its CUDA graph
+// (captured on its first repeat); a new set runs eagerly.  Graphs bake in the
+// pointers and schedules, which form the key.
+nm_status run_items(const std::vector<Item>& items, cudaStream_t s) {
+    std::vector<const void*> key;
+    for (const Item& it : items) {
+        key.push_back(it.p);
+        key.push_back(it.rho);
+        key.push_back(it.phi);
+        const nm_schedule& sc = it.p->sched;
+        key.push_back((const void*)(uintptr_t)((sc.group << 12) | (sc.radix << 3) | (sc.fuse << 2) |
+                                               (sc.tile << 1) | sc.pipeline));
+    }
+    for (const Item& it : items) {
+        nm_status st = ensure_green(it.p, s);
+        if (st != NM_OK) return st;
+    }
+    if (g_prof_on.load() || fault_timeout_on() || env_int("NM_NO_GRAPHS", 0)) return enqueue_all(items, s);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+        return enqueue_all(items, s);             // the caller is capturing: just record
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;
+    bool seen = false;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (size_t i = 0; i < g_graphs.size(); ++i)
+            if (g_graphs[i].key == key) {
+                seen = true;
+                exec = g_graphs[i].exec;
+                kernels = g_graphs[i].kernels;
+                BatchGraph g = g_graphs[i];
+                g_graphs.erase(g_graphs.begin() + i);
+                g_graphs.push_back(g);
+                break;
+            }
+        if (!seen) {
+            if (g_graphs.size() >= kMaxGraphs) {
+                if (g_graphs.front().exec) cudaGraphExecDestroy(g_graphs.front().exec);
+                g_graphs.erase(g_graphs.begin());
+            }
+            g_graphs.push_back(BatchGraph{key, nullptr, false});
+        }
+    }
+    if (!seen) return enqueue_all(items, s);
+    if (!exec) {
+        cudaStream_t cs;
+        NM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        nm_status st = NM_OK;
+        const uint64_t before = g_launches.load();
+        if (e == cudaSuccess) {
+            st = enqueue_all(items, cs);
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        // recorded, not launched: the replay below counts them
+        kernels = g_launches.load() - before;
+        g_launches.fetch_sub(kernels);
+        if (e == cudaSuccess && st == NM_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (st != NM_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (auto& g : g_graphs)
+            if (g.key == key) {
+                g.exec = exec;
+                g.captured = true;
+                g.kernels = kernels;
+            }
+    }
+    NM_CUDA(cudaGraphLaunch(exec, s), "graph launch");
+    count_launches((int)kernels);
+    return NM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -862,7 +941,7 @@ nm_status nm_potential(nm_plan_t p, const void* rho, double* phi, void* stream) 
     if (!p || !rho || !phi) return fail(NM_EINVAL, "nm_potential: null argument");
     if (((uintptr_t)phi & 15) || ((uintptr_t)rho & (p->es - 1)))
         return fail(NM_EINVAL, "nm_potential: phi must be 16-byte aligned and rho element aligned");
-    return potential_impl(p, rho, phi, (cudaStream_t)stream);
+    return run_items({Item{p, rho, phi}}, (cudaStream_t)stream);
 }
 
 nm_status nm_potential_host(nm_plan_t p, const void* rho_host, double* phi_host, void* stream) {
@@ -875,7 +954,7 @@ nm_status nm_potential_host(nm_plan_t p, const void* rho_host, double* phi_host,
         p->ws_bytes += cells * (p->es + sizeof(double));
     }
     NM_CUDA(cudaMemcpyAsync(p->h_rho, rho_host, cells * p->es, cudaMemcpyHostToDevice, s), "rho upload");
-    nm_status st = potential_impl(p, p->h_rho, p->h_phi, s);
+    nm_status st = run_items({Item{p, p->h_rho, p->h_phi}}, s);
     if (st != NM_OK) return st;
     NM_CUDA(cudaMemcpyAsync(phi_host, p->h_phi, cells * sizeof(double), cudaMemcpyDeviceToHost, s), "phi download");
     NM_CUDA(cudaStreamSynchronize(s), "nm_potential_host sync");
@@ -888,7 +967,6 @@ nm_status nm_batch_potential(int n, const nm_plan_t* plans, const void* const* r
     int dev = 0;
     NM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     std::vector<Item> items;
-    std::vector<const void*> key;
     for (int i = 0; i < n; ++i) {
         if (!plans[i] || !rho[i] || !phi[i]) return fail(NM_EINVAL, "nm_batch_potential: null entry %d", i);
         if ((uintptr_t)phi[i] & 15) return fail(NM_EINVAL, "nm_batch_potential: phi %d not 16-byte aligned", i);
@@ -896,65 +974,9 @@ nm_status nm_batch_potential(int n, const nm_plan_t* plans, const void* const* r
         for (int k = 0; k < i; ++k)
             if (plans[k] == plans[i]) return fail(NM_EINVAL, "nm_batch_potential: plan %d repeated", i);
         items.push_back({plans[i], rho[i], phi[i]});
-        key.push_back(plans[i]);
-        key.push_back(rho[i]);
-        key.push_back(phi[i]);
-        key.push_back((const void*)(uintptr_t)((plans[i]->sched.group << 12) | (plans[i]->sched.radix << 3) |
-                                               (plans[i]->sched.fuse << 2) | (plans[i]->sched.tile << 1) |
-                                               plans[i]->sched.pipeline));
     }
     if (n == 0) return NM_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    for (auto& it : items) {
-        nm_status st = ensure_green(it.p, s);
-        if (st != NM_OK) return st;
-    }
-    if (g_prof_on.load() || fault_timeout_on() || env_int("NM_NO_GRAPHS", 0)) return enqueue_all(items, s);
-    // repeated batch: replay its graph; first repeat: capture it
-    cudaGraphExec_t exec = nullptr;
-    bool seen = false;
-    {
-        std::lock_guard<std::mutex> lk(g_graph_mu);
-        for (size_t i = 0; i < g_graphs.size(); ++i)
-            if (g_graphs[i].key == key) {
-                seen = true;
-                exec = g_graphs[i].exec;
-                BatchGraph g = g_graphs[i];
-                g_graphs.erase(g_graphs.begin() + i);
-                g_graphs.push_back(g);
-                break;
-            }
-    }
-    if (!seen) {
-        std::lock_guard<std::mutex> lk(g_graph_mu);
-        if (g_graphs.size() >= kMaxGraphs) {
-            if (g_graphs.front().exec) cudaGraphExecDestroy(g_graphs.front().exec);
-            g_graphs.erase(g_graphs.begin());
-        }
-        g_graphs.push_back(BatchGraph{key, nullptr, false});
-    }
-    if (!seen) return enqueue_all(items, s);
-    if (!exec) {
-        cudaStream_t cs;
-        NM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        nm_status st = NM_OK;
-        if (e == cudaSuccess) {
-            st = enqueue_all(items, cs);
-            e = cudaStreamEndCapture(cs, &graph);
-        }
-        if (e == cudaSuccess && st == NM_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-        if (st != NM_OK) return st;
-        if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
-        std::lock_guard<std::mutex> lk(g_graph_mu);
-        for (auto& g : g_graphs)
-            if (g.key == key) { g.exec = exec; g.captured = true; }
-    }
-    NM_CUDA(cudaGraphLaunch(exec, s), "batch graph launch");
-    return NM_OK;
+    return run_items(items, (cudaStream_t)stream);
 }
 
 nm_status nm_get_schedule(nm_plan_t p, nm_schedule* out) {

@@ -81,6 +81,25 @@ __device__ __forceinline__ T src_value(const SrcField& f, T scale, int NL, int z
     return v * scale;
 }
 
+// Both fields of a pair at block cell (z, y, x), scaled.  When the pair is a
+// level's full and hole grids (Fig. 5) the density is loaded once.
+template <typename T, typename TIN>
+__device__ __forceinline__ cpx<T> src_pair(const SrcField& f0, const SrcField& f1, T s0, T s1, int NL,
+                                           int z, int y, int x) {
+    if (f0.mode == SRC_FULL && f1.mode == SRC_HOLE && f0.rho == f1.rho) {
+        const int q = NL / 4, h = NL / 2;
+        const bool cov = (unsigned)(z - q) < (unsigned)h && (unsigned)(y - q) < (unsigned)h &&
+                         (unsigned)(x - q) < (unsigned)h;
+        T v;
+        if (cov && f0.restr)
+            v = (T)((const TIN*)f0.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)];
+        else
+            v = (T)((const TIN*)f0.rho)[((size_t)z * NL + y) * NL + x];
+        return {v * s0, cov ? T(0) : v * s1};
+    }
+    return {src_value<T, TIN>(f0, s0, NL, z, y, x), src_value<T, TIN>(f1, s1, NL, z, y, x)};
+}
+
 template <int P, int E, bool DBL> struct Geo {
     static constexpr int NIN = DBL ? P / 4 : P / 2;   // input block extent
     static constexpr int OFF = DBL ? P / 8 : 0;       // its offset in the domain
@@ -113,8 +132,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
         v[r] = {T(0), T(0)};
         if (G::live(r) && valid) {
             const int xi = j + r * (P / E) - G::OFF;
-            v[r].re = src_value<T, TIN>(d.src[0], s0, G::NIN, zi, yi, xi);
-            v[r].im = src_value<T, TIN>(d.src[1], s1, G::NIN, zi, yi, xi);
+            v[r] = src_pair<T, TIN>(d.src[0], d.src[1], s0, s1, G::NIN, zi, yi, xi);
         }
     }
     __syncthreads();

@@ -80,8 +80,7 @@ __global__ void __cluster_dims__(FusedShape<T, P>::C, 1, 1) __launch_bounds__(Fu
                 v[r] = {T(0), T(0)};
                 if (r < E / 2 && valid) {
                     const int x = j + r * (P / E);
-                    v[r].re = src_value<T, TIN>(d.src[0], s0, N, z, y, x);
-                    v[r].im = src_value<T, TIN>(d.src[1], s1, N, z, y, x);
+                    v[r] = src_pair<T, TIN>(d.src[0], d.src[1], s0, s1, N, z, y, x);
                 }
             }
             fft_line<T, P, E, false>(v, j, sm_tw,

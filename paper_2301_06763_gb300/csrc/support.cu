@@ -245,13 +245,109 @@ __global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
     }
 }
 
+// The stencil weight of axis_stencil in float (a dyadic fraction with at most
+// 16 bits, so exact), widened to T without the FP64 pipe.
+__device__ __forceinline__ float stencil_weight(int N, int lgr, int i, int& i0) {
+    const int num = (N - 1) * ((1 << lgr) - 1) + 2 * i;
+    i0 = num >> (lgr + 1);
+    return (float)(num & ((2 << lgr) - 1)) * (1.0f / (float)(2 << lgr));
+}
+template <typename T> __device__ __forceinline__ T as_t(float f);
+template <> __device__ __forceinline__ float as_t<float>(float f) { return f; }
+template <> __device__ __forceinline__ double as_t<double>(float f) { return widen(f); }
+
+// Row-wise assembly (N >= 16): a team of N/4 threads owns one fine row
+// (level n, z, y), 4 cells per thread.  For each coarser level k the row's
+// z and y stencils are fixed, so the team first interpolates bilinearly in
+// (z, y) at every coarse x the row needs (N/2^(n-k) + 2 values) into shared
+// memory, then each cell interpolates linearly along x from there: the same
+// trilinear value with about a third of the loads and arithmetic.
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble_rows(const __grid_constant__ AssembleArgs<T> a, int lgN) {
+    const int N = 1 << lgN;
+    const int team = N >> 2;                 // threads per fine row
+    const int rows_cta = 256 / team;         // rows per CTA (divides N^2 for N >= 16)
+    const int crw = N / 2 + 2;               // coarse values per row, at most
+    const int tr = threadIdx.x / team, tl = threadIdx.x % team;
+    const int x0 = 4 * tl;
+    extern __shared__ __align__(16) unsigned char smem_rows[];
+    T* cr = reinterpret_cast<T*>(smem_rows) + tr * crw;
+    const size_t N2 = (size_t)1 << (2 * lgN);
+    const size_t rows_total = N2 * a.levels;
+    for (size_t rb = (size_t)blockIdx.x * rows_cta; rb < rows_total; rb += (size_t)gridDim.x * rows_cta) {
+        const int n = (int)(rb >> (2 * lgN));            // same level for the whole batch
+        const size_t zy = rb + tr - ((size_t)n << (2 * lgN));
+        const int z = (int)(zy >> lgN), y = (int)(zy & (N - 1));
+        const size_t cell = (zy << lgN) + x0;
+        T b[4];
+        Vec4<T>::load(a.base[n] + cell, b);
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        if (a.dbl[n]) {
+            const int E = 2 * N;
+            const T* d = a.dbl[n];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                T s = T(0);
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy) {
+                        const T* row = d + ((size_t)(2 * z + dz) * E + (2 * y + dy)) * E + 2 * (x0 + c);
+                        s += row[0] + row[1];
+                    }
+                acc[c] += s * T(0.125);
+            }
+        }
+        for (int k = 0; k < n; ++k) {
+            const int lgr = n - k;
+            int iz, iy, lo, hi;
+            const T tz = as_t<T>(stencil_weight(N, lgr, z, iz));
+            const T ty = as_t<T>(stencil_weight(N, lgr, y, iy));
+            stencil_weight(N, lgr, 0, lo);
+            stencil_weight(N, lgr, N - 1, hi);
+            const int cnt = hi - lo + 2;
+            const int o = a.interp_origin[k], E = a.interp_extent[k];
+            const size_t sz = (size_t)E * E, sy = E;
+            const T* src = a.interp[k] + ((size_t)(iz - o) * E + (iy - o)) * E - o;
+            for (int i = tl; i < cnt; i += team) {
+                const T* p = src + lo + i;
+                const T c0 = p[0] + ty * (p[sy] - p[0]);
+                const T c1 = p[sz] + ty * (p[sz + sy] - p[sz]);
+                cr[i] = c0 + tz * (c1 - c0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                int ix;
+                const T tx = as_t<T>(stencil_weight(N, lgr, x0 + c, ix));
+                const T* q = cr + (ix - lo);
+                acc[c] += q[0] + tx * (q[1] - q[0]);
+            }
+            __syncthreads();
+        }
+        double2* out = reinterpret_cast<double2*>(a.phi + ((size_t)n << (3 * lgN)) + cell);
+        out[0] = make_double2(widen(b[0]) + widen(acc[0]), widen(b[1]) + widen(acc[1]));
+        out[1] = make_double2(widen(b[2]) + widen(acc[2]), widen(b[3]) + widen(acc[3]));
+    }
+}
+
 template <typename T>
 cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
-    const size_t total = (size_t)a.N * a.N * a.N * a.levels / 4;
-    size_t blocks = (total + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
     ProfScope ps(sizeof(T) == 4 ? "assemble_f32" : "assemble_f64", a.levels, s);
-    k_assemble<T><<<(int)blocks, 256, 0, s>>>(a, ilog2(a.N));
+    const int lgN = ilog2(a.N);
+    if (a.N >= 16) {
+        const int team = a.N / 4, rows_cta = 256 / team;
+        const size_t rows = (size_t)a.N * a.N * a.levels;
+        size_t blocks = rows / rows_cta;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        const size_t smem = (size_t)rows_cta * (a.N / 2 + 2) * sizeof(T);
+        k_assemble_rows<T><<<(int)blocks, 256, smem, s>>>(a, lgN);
+    } else {
+        const size_t total = (size_t)a.N * a.N * a.N * a.levels / 4;
+        size_t blocks = (total + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        k_assemble<T><<<(int)blocks, 256, 0, s>>>(a, lgN);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
