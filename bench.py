@@ -460,7 +460,7 @@ def serve_mode(args):
         w = wl.Workload("serve-%d" % N, 10, N, 1.0 / N, wl.random_plummers(rng, 10, N))
         dens[N] = torch.from_numpy(np.ascontiguousarray(w.rho().astype(np.float32))).pin_memory()
     free, total = torch.cuda.mem_get_info()
-    budget = int(0.6 * free)
+    budget = int(0.5 * free)
     results = []
     for rate in [float(x) for x in args.rates.split(",")]:
         count = int(min(2000, max(20, rate * args.serve_seconds)))
@@ -481,6 +481,7 @@ def serve_mode(args):
                         "failed": len(srv.failed), "solves_per_s": len(done) / elapsed,
                         "batches": srv.batches, "peak_bytes": srv.peak_used, **st})
         srv.close()
+        torch.cuda.empty_cache()
     print(json.dumps({"mode": "serve", "metric": "served solves/s and latency (arrival -> host potentials)",
                       "unit": "solves/s", "budget_bytes": budget, "precision": "fp32",
                       "requests": "N in {32,64,128,256}, 3-10 levels, Poisson arrivals",

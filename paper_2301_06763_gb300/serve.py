@@ -130,6 +130,8 @@ class Server:
             plan, need_plan = self._take_plan(r)
             try:
                 need = self.request_bytes(r, with_plan=need_plan)
+                if plan is not None:        # a pooled plan's workspace moves from the pool to `used`
+                    need += plan.workspace_bytes()
             except Exception as e:          # invalid shape: rejected by the library
                 self.queue.popleft()
                 r.error = str(e)
