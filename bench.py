@@ -245,11 +245,8 @@ def timed_loop(torch, plan, rhos, phis, steps, dist, stream):
 
 
 def max_over_ranks(torch, dist, v):
-    if dist is None:
-        return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2301_06763_gb300 import replicas
+    return replicas.max_over_ranks(v, dist, device="cuda" if dist is not None else None)
 
 
 def pct(xs, q):
@@ -328,8 +325,9 @@ def ours(args):
             dist.destroy_process_group()
         return
 
+    from paper_2301_06763_gb300 import replicas
     ms_step = dev_ms / args.steps
-    value = world * args.steps / (dev_ms / 1e3)
+    value = replicas.job_rate(world * args.steps, dev_ms / 1e3)
     peak, peak_kind = peaks()
     dom = max(stats.items(), key=lambda kv: kv[1][2])
     dname, (dl, du, dms) = dom
