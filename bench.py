@@ -244,6 +244,33 @@ def timed_loop(torch, plan, rhos, phis, steps, dist, stream):
     return total_dev_ms, per, elapsed_wall
 
 
+def dipole_rates(nm, wl, torch, dev, reps=20):
+    """Pairwise dipole method (Sect. 7, Eqs. B.1-B.2) on 4 levels of 64^3 (two
+    Plummer spheres), against the original method on the same mesh."""
+    w = wl.config_binary()
+    rho = w.rho()
+    out = {"workload": "binary-4x64"}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        r = torch.from_numpy(rho).to(dev, dt)
+        phi = torch.empty(rho.shape, dtype=torch.float64, device=dev)
+        for meth in ("original", "dipole"):
+            p = nm.Plan(w.levels, w.N, w.dx0, precision=prec, method=meth)
+            n = reps if prec == "fp32" else max(2, reps // 5)
+            for _ in range(3):
+                p.potential(r, phi)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(n):
+                p.potential(r, phi)
+            b.record()
+            torch.cuda.synchronize()
+            out["%s_%s_ms" % (meth, prec)] = a.elapsed_time(b) / n
+            p.close()
+        out["overhead_%s" % prec] = out["dipole_%s_ms" % prec] / out["original_%s_ms" % prec]
+    return out
+
+
 def max_over_ranks(torch, dist, v):
     from paper_2301_06763_gb300 import replicas
     return replicas.max_over_ranks(v, dist, device="cuda" if dist is not None else None)
@@ -346,6 +373,7 @@ def ours(args):
                       if pass_bytes(k, N, True) is not None) / args.steps
     kernel_table = {k: {"launches": v[0], "avg_ms": v[2] / v[0], "share": v[2] / sum(
         x[2] for x in stats.values())} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][2])}
+    dip = dipole_rates(nm, wl, torch, dev) if not args.no_cpu_baseline else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(L, N)
@@ -373,6 +401,7 @@ def ours(args):
         "roofline": roof,
         "kernels": kernel_table,
         "cpu_baseline": cpu,
+        "dipole": dip,
         "clocks": clk,
     }
     print(json.dumps(line))

@@ -122,17 +122,56 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
     const PairDesc<T>& d = a.pair[blockIdx.y];
     load_twiddles(sm_tw, a.tw, P);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
-    const int row = blockIdx.x * LINES + line;
+    const int row0 = blockIdx.x * LINES;
+    const int row = row0 + line;
     const bool valid = row < G::NIN * G::NIN;
     const int zi = row / G::NIN, yi = row % G::NIN;
     const T s0 = (T)d.src[0].scale, s1 = (T)d.src[1].scale;
     cpx<T> v[E];
+    // A level's full and hole grids share one density: the CTA's rows are
+    // contiguous in it, so stage them through shared memory with 16-byte
+    // loads (more bytes in flight per instruction than the transform's
+    // strided layout allows) and read the transform layout from there.
+    const bool staged = !DBL && d.src[0].mode == SRC_FULL && d.src[0].rho == d.src[1].rho &&
+                        (d.src[1].mode == SRC_HOLE || d.src[1].mode == SRC_NONE) &&
+                        (((uintptr_t)d.src[0].rho & 15) == 0);
+    if (staged) {
+        constexpr int NIN = G::NIN, VEC = 16 / sizeof(TIN);
+        T* stage = reinterpret_cast<T*>(sm_lines);
+        const int rows = min(LINES, NIN * NIN - row0);
+        const TIN* base = (const TIN*)d.src[0].rho + (size_t)row0 * NIN;
+        for (int i = threadIdx.x * VEC; i < rows * NIN; i += blockDim.x * VEC) {
+            TIN tmp[VEC];
+            *reinterpret_cast<int4*>(tmp) = __ldg(reinterpret_cast<const int4*>(base + i));
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        v[r] = {T(0), T(0)};
-        if (G::live(r) && valid) {
-            const int xi = j + r * (P / E) - G::OFF;
-            v[r] = src_pair<T, TIN>(d.src[0], d.src[1], s0, s1, G::NIN, zi, yi, xi);
+            for (int q = 0; q < VEC; ++q) stage[i + q] = (T)tmp[q];
+        }
+        __syncthreads();
+        const int q = NIN / 4, h = NIN / 2;
+        const bool row_cov = (unsigned)(zi - q) < (unsigned)h && (unsigned)(yi - q) < (unsigned)h;
+        const bool hole = d.src[1].mode == SRC_HOLE;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = {T(0), T(0)};
+            if (G::live(r) && valid) {
+                const int xi = j + r * (P / E);
+                const T val = stage[line * NIN + xi];
+                const bool cov = row_cov && (unsigned)(xi - q) < (unsigned)h;
+                T full = val;
+                if (cov && d.src[0].restr)
+                    full = (T)((const TIN*)d.src[0].restr)[((size_t)(zi - q) * h + (yi - q)) * h + (xi - q)];
+                v[r].re = full * s0;
+                v[r].im = (hole && !cov) ? val * s1 : T(0);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = {T(0), T(0)};
+            if (G::live(r) && valid) {
+                const int xi = j + r * (P / E) - G::OFF;
+                v[r] = src_pair<T, TIN>(d.src[0], d.src[1], s0, s1, G::NIN, zi, yi, xi);
+            }
         }
     }
     __syncthreads();

@@ -40,12 +40,65 @@ __global__ void k_restrict(const TIN* __restrict__ rho_child, const TIN* __restr
     }
 }
 
+// Two adjacent outputs per thread (N >= 16): their 2 x 2 x 4 children are
+// contiguous runs of 4 along x, read as 16-byte vectors, and the 8 children of
+// each output are either all covered by the next level or none (the covered
+// range [N/4, 3N/4) starts and ends on even indices), the same for both.
+template <typename TIN> struct Vec4In;
+template <> struct Vec4In<float> {
+    static __device__ __forceinline__ void load(const float* p, float* v) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+};
+template <> struct Vec4In<double> {
+    static __device__ __forceinline__ void load(const double* p, double* v) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
+template <typename TIN>
+__global__ void k_restrict2(const TIN* __restrict__ rho_child, const TIN* __restrict__ restr_child,
+                            TIN* __restrict__ out, int lgN) {
+    const int N = 1 << lgN, h = N / 2, q = N / 4, lgh = lgN - 1;
+    const int n = (h * h * h) / 2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = 2 * (i & (h / 2 - 1)), b = (i >> (lgh - 1)) & (h - 1), a = i >> (2 * lgh - 1);
+        TIN s0 = TIN(0), s1 = TIN(0);
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy) {
+                const int z = 2 * a + dz, y = 2 * b + dy, x = 2 * c;
+                const bool cov = restr_child && (unsigned)(z - q) < (unsigned)h &&
+                                 (unsigned)(y - q) < (unsigned)h && (unsigned)(x - q) < (unsigned)h;
+                TIN w[4];
+                if (cov)
+                    Vec4In<TIN>::load(restr_child + ((size_t)(z - q) * h + (y - q)) * h + (x - q), w);
+                else
+                    Vec4In<TIN>::load(rho_child + ((size_t)z * N + y) * N + x, w);
+                s0 += w[0] + w[1];
+                s1 += w[2] + w[3];
+            }
+        out[2 * i] = s0 * TIN(0.125);
+        out[2 * i + 1] = s1 * TIN(0.125);
+    }
+}
+
 template <typename TIN>
 cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* restr_out, int N,
                          cudaStream_t s) {
     const int n = (N / 2) * (N / 2) * (N / 2);
-    const int blocks = (n + 255) / 256;
     ProfScope ps(sizeof(TIN) == 4 ? "restrict_f32" : "restrict_f64", 1, s);
+    const bool vec = N >= 16 && ((uintptr_t)rho_child & 15) == 0 && ((uintptr_t)restr_child & 15) == 0;
+    if (vec) {
+        k_restrict2<TIN><<<(n / 2 + 255) / 256, 256, 0, s>>>(rho_child, restr_child, restr_out, ilog2(N));
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    const int blocks = (n + 255) / 256;
     k_restrict<TIN><<<blocks, 256, 0, s>>>(rho_child, restr_child, restr_out, ilog2(N));
     count_launches(1);
     return cudaGetLastError();
