@@ -178,3 +178,42 @@ def random_density(seed, levels, N, positive=True):
     rng = np.random.default_rng(seed)
     r = rng.random((levels, N, N, N))
     return r if positive else r - 0.5
+
+
+# --- the paper's comparison problems (Sect. 2 and Sect. 5) ------------------------
+
+@dataclass(frozen=True)
+class HomogeneousSpheroid:
+    """Uniform density inside x^2/a^2 + y^2/a^2 + z^2/c^2 <= 1."""
+    a: float
+    c: float
+    rho: float = 1.0
+
+    def density(self, x, y, z):
+        inside = (x * x + y * y) / self.a ** 2 + z * z / self.c ** 2 <= 1.0
+        return np.where(inside, self.rho, 0.0)
+
+
+@dataclass(frozen=True)
+class HomogeneousSphere:
+    radius: float
+    rho: float
+    centre: tuple = (0.0, 0.0, 0.0)
+
+    def density(self, x, y, z):
+        cx, cy, cz = self.centre
+        r2 = (x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2
+        return np.where(r2 <= self.radius ** 2, self.rho, 0.0)
+
+
+def config_paper_ellipsoid(N=128, levels=4):
+    """Oblate homogeneous ellipsoid with semi-axes 1 : 1 : 0.5 (short axis on z)
+    in the domain [-2.25, 2.25]^3, the paper's first test problem."""
+    return Workload("ellipsoid-%dx%d" % (levels, N), levels, N, 4.5 / N, [HomogeneousSpheroid(1.0, 0.5)])
+
+
+def config_paper_binary(N=128, levels=4):
+    """Two homogeneous spheres of radius 0.2 centred at x = -0.5 and x = +0.5,
+    the left one twice as massive, in [-2.25, 2.25]^3: the paper's binary star."""
+    return Workload("binary-star-%dx%d" % (levels, N), levels, N, 4.5 / N, [
+        HomogeneousSphere(0.2, 2.0, (-0.5, 0.0, 0.0)), HomogeneousSphere(0.2, 1.0, (0.5, 0.0, 0.0))])

@@ -71,3 +71,33 @@ def box_integral(px, py, pz, x1, x2, y1, y2, z1, z2):
                 s = 1.0 if (i + j + k) % 2 == 1 else -1.0
                 tot += s * F(X, Y, Z)
     return tot
+
+
+def oblate_spheroid(x, y, z, a, c, rho=1.0, G=1.0):
+    """Homogeneous oblate spheroid x^2/a^2 + y^2/a^2 + z^2/c^2 <= 1 (a > c).
+
+    Classical ellipsoid potential (Chandrasekhar 1969):
+      Phi = -pi G rho a^2 c [J0 - (x^2 + y^2) J1 - z^2 J3],
+      J0 = int_l^inf du / D(u),  J1 = int du / ((a^2+u) D),  J3 = int du / ((c^2+u) D),
+      D(u) = (a^2 + u) sqrt(c^2 + u),
+    with l = 0 inside and, outside, the positive root of
+    (x^2 + y^2)/(a^2 + l) + z^2/(c^2 + l) = 1.  With s = sqrt(c^2 + u) and
+    e2 = a^2 - c^2 the integrals are elementary (s0 = sqrt(c^2 + l)):
+      J0 = 2/sqrt(e2) atan(sqrt(e2)/s0)
+      J1 = atan(sqrt(e2)/s0)/e2^1.5 - s0/(e2 (e2 + s0^2))
+      J3 = 2/(e2 s0) - 2 atan(sqrt(e2)/s0)/e2^1.5
+    """
+    x, y, z = (np.asarray(v, dtype=float) for v in (x, y, z))
+    R2 = x * x + y * y
+    z2 = z * z
+    B = a * a + c * c - R2 - z2
+    C = a * a * c * c - R2 * c * c - z2 * a * a
+    disc = np.sqrt(np.maximum(B * B - 4.0 * C, 0.0))
+    lam = np.where(R2 / (a * a) + z2 / (c * c) <= 1.0, 0.0, 0.5 * (-B + disc))
+    e2 = a * a - c * c
+    s0 = np.sqrt(c * c + lam)
+    at = np.arctan(np.sqrt(e2) / s0)
+    J0 = 2.0 / np.sqrt(e2) * at
+    J1 = at / e2 ** 1.5 - s0 / (e2 * (e2 + s0 * s0))
+    J3 = 2.0 / (e2 * s0) - 2.0 * at / e2 ** 1.5
+    return -math.pi * G * rho * a * a * c * (J0 - R2 * J1 - z2 * J3)
