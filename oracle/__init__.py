@@ -15,6 +15,8 @@ It is a plain, slow, step-by-step restatement of the method in float64 numpy:
 * ``nested``      -- restriction, hole grids, trilinear interpolation and the
                      assembly of Eq. 14 (Sect. 4), plus the pairwise-dipole
                      variant of Eqs. 15 and B.1-B.2 (Sect. 7, Appendix B).
+* ``acceleration``-- g = -grad Phi with the six-point stencil of Eq. 8 and the
+                     interface rules of Sect. 2 / Appendix A (methods A, B).
 * ``direct``      -- a second route to the same nested potential at sampled
                      cells using direct summation only (no FFT), for checks at
                      sizes where the FFT oracle is too slow.
@@ -29,9 +31,10 @@ from .convolution import isolated_convolution, direct_sum
 from .nested import (Geometry, restrict, level_masses, solve, trilinear_to_level,
                      solve_components)
 from .direct import nested_potential_at
+from .acceleration import acceleration
 
 __all__ = [
     "fft_axis", "fft3", "ifft3", "SELF_TERM_C", "green_kernel", "green_spectrum",
     "isolated_convolution", "direct_sum", "Geometry", "restrict", "level_masses",
-    "solve", "solve_components", "trilinear_to_level", "nested_potential_at",
+    "solve", "solve_components", "trilinear_to_level", "nested_potential_at", "acceleration",
 ]

@@ -101,3 +101,38 @@ def oblate_spheroid(x, y, z, a, c, rho=1.0, G=1.0):
     J1 = at / e2 ** 1.5 - s0 / (e2 * (e2 + s0 * s0))
     J3 = 2.0 / (e2 * s0) - 2.0 * at / e2 ** 1.5
     return -math.pi * G * rho * a * a * c * (J0 - R2 * J1 - z2 * J3)
+
+
+def oblate_spheroid_accel(x, y, z, a, c, rho=1.0, G=1.0):
+    """g = -grad Phi of `oblate_spheroid`: the derivative through the lower
+    limit vanishes (the integrand is zero there), so
+    g = -2 pi G rho a^2 c (x J1, y J1, z J3)."""
+    x, y, z = (np.asarray(v, dtype=float) for v in (x, y, z))
+    R2, z2 = x * x + y * y, z * z
+    B = a * a + c * c - R2 - z2
+    C = a * a * c * c - R2 * c * c - z2 * a * a
+    disc = np.sqrt(np.maximum(B * B - 4.0 * C, 0.0))
+    lam = np.where(R2 / (a * a) + z2 / (c * c) <= 1.0, 0.0, 0.5 * (-B + disc))
+    e2 = a * a - c * c
+    s0 = np.sqrt(c * c + lam)
+    at = np.arctan(np.sqrt(e2) / s0)
+    J1 = at / e2 ** 1.5 - s0 / (e2 * (e2 + s0 * s0))
+    J3 = 2.0 / (e2 * s0) - 2.0 * at / e2 ** 1.5
+    k = -2.0 * math.pi * G * rho * a * a * c
+    return k * x * J1, k * y * J1, k * z * J3
+
+
+def sphere_accel(dx, dy, dz, M, R, G=1.0):
+    """Uniform sphere: g = -G M r_vec / R^3 inside, -G M r_vec / r^3 outside."""
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    f = np.where(r <= R, -G * M / R ** 3, -G * M / np.maximum(r, 1e-300) ** 3)
+    return f * dx, f * dy, f * dz
+
+
+def poly_sphere_accel_radial(r, M, R, G=1.0):
+    """|g| of the C^1 polynomial sphere: G M(<r) / r^2."""
+    r = np.asarray(r, dtype=float)
+    rho0 = M / (4.0 * math.pi * R ** 3 * 8.0 / 105.0)
+    s = np.clip(r / R, 0.0, 1.0)
+    m_in = 4.0 * math.pi * rho0 * R ** 3 * (s ** 3 / 3.0 - 2.0 * s ** 5 / 5.0 + s ** 7 / 7.0)
+    return G * m_in / np.maximum(r, 1e-300) ** 2
