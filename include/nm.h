@@ -125,6 +125,18 @@ nm_status nm_green(nm_plan_t plan, void* stream);
  * caller's own stream capture the kernels are simply recorded. */
 nm_status nm_potential(nm_plan_t plan, const void* rho, double* phi, void* stream);
 
+/* Gravitational acceleration g = -grad Phi of a nested potential `phi`
+ * (device, L*N^3 doubles, as written by nm_potential for this plan's mesh)
+ * into `g` (device, L*3*N^3 doubles, [level][component x,y,z][z][y][x]),
+ * asynchronously on `stream`.  Central six-point differences (Eq. 8) on every
+ * level; at the boundary of a finer level the missing neighbour is the ghost
+ * value interpolated from the coarser level by Eqs. 3-6 (method A of
+ * Appendix A); an uncovered coarse cell next to the finer level takes the mean
+ * of the 2^3 finer children for its covered neighbour (method B); the outer
+ * boundary of the coarsest level uses second-order one-sided differences.
+ * In double precision for both plan precisions. */
+nm_status nm_acceleration(nm_plan_t plan, const double* phi, double* g, void* stream);
+
 /* Same result from HOST buffers: copies rho to the device, solves, copies phi
  * back, all on `stream`, and waits for the stream before returning.  Host
  * buffers in pinned memory give asynchronous copies. */

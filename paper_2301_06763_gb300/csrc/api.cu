@@ -1045,6 +1045,13 @@ nm_status nm_autotune(nm_plan_t p, const void* rho, double* phi, int reps, void*
     return NM_OK;
 }
 
+nm_status nm_acceleration(nm_plan_t p, const double* phi, double* g, void* stream) {
+    if (!p || !phi || !g) return fail(NM_EINVAL, "nm_acceleration: null argument");
+    cudaError_t e = run_accel(phi, g, p->L, p->N, p->opt.dx0, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "acceleration");
+    return NM_OK;
+}
+
 nm_status nm_workspace_bytes(nm_plan_t p, size_t* bytes) {
     if (!p || !bytes) return fail(NM_EINVAL, "nm_workspace_bytes: null argument");
     *bytes = p->ws_bytes;

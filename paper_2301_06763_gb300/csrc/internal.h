@@ -71,4 +71,7 @@ template <typename T> struct AssembleArgs {
 template <typename T>
 cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s);
 
+// g = -grad Phi of a nested potential (accel.cu).
+cudaError_t run_accel(const double* phi, double* g, int levels, int N, double dx0, cudaStream_t s);
+
 }  // namespace nm

@@ -70,6 +70,7 @@ def lib():
             "nm_green": (st, [P, P]),
             "nm_potential": (st, [P, P, P, P]),
             "nm_potential_host": (st, [P, P, P, P]),
+            "nm_acceleration": (st, [P, P, P, P]),
             "nm_workspace_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "nm_spectrum_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "nm_batch_potential": (st, [ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P),
@@ -211,6 +212,19 @@ class Plan:
         _check(lib().nm_potential(self.handle, ctypes.c_void_p(rho.data_ptr()),
                                   ctypes.c_void_p(phi.data_ptr()), _stream_handle(stream)))
         return phi
+
+    def acceleration(self, phi, g=None, stream=None):
+        """g = -grad Phi ((levels, 3, N, N, N) float64) of a potential from ``potential``."""
+        import torch
+        self._check_tensor(phi, torch.float64, "phi")
+        if g is None:
+            g = torch.empty((self.levels, 3, self.N, self.N, self.N), dtype=torch.float64, device=phi.device)
+        if g.dtype != torch.float64 or tuple(g.shape) != (self.levels, 3, self.N, self.N, self.N) \
+                or not g.is_contiguous() or not g.is_cuda:
+            raise ValueError("g must be a contiguous CUDA float64 tensor of shape (levels, 3, N, N, N)")
+        _check(lib().nm_acceleration(self.handle, ctypes.c_void_p(phi.data_ptr()),
+                                     ctypes.c_void_p(g.data_ptr()), _stream_handle(stream)))
+        return g
 
     def potential_host(self, rho, phi=None, stream=None):
         """Solve from host memory (numpy arrays or CPU tensors); synchronous."""

@@ -57,6 +57,7 @@ def test_plan_rejects_bad_geometry_before_touching_the_device(lib, levels, N, dx
 def test_null_arguments(lib):
     assert lib.nm_plan_ex(None, None) == 1
     assert lib.nm_potential(None, None, None, None) == 1
+    assert lib.nm_acceleration(None, None, None, None) == 1
     assert lib.nm_destroy(None) == 1
     assert lib.nm_batch_potential(-1, None, None, None, None) == 1
     o = __import__("paper_2301_06763_gb300.nm", fromlist=["Options"]).Options()
