@@ -11,16 +11,42 @@ Test infrastructure only; see the package docstring.
 import numpy as np
 
 from .convolution import direct_sum_at
+from .acceleration import ghost_index
 from .nested import Geometry, interp_coords, level_masses, restrict
 
 
-def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original"):
-    """Phi(Omega^n) at cells ``samples`` = iterable of (n, z, y, x)."""
+def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original", interp="trilinear"):
+    """Phi(Omega^n) at cells ``samples`` = iterable of (n, z, y, x).
+
+    interp='diagonal' evaluates the carried hole term of the Eqs. 3-6 reading
+    recursively: carry_n(i) = 3/4 S_{n-1}(c) + 1/4 S_{n-1}(c + s), with
+    S_k = Phi^k_hole + carry_k and (c, s) the nearest coarse cell and the
+    diagonal step of fine cell i, every Phi^k_hole value a direct sum."""
     rho = np.asarray(rho, dtype=np.float64)
     L = rho.shape[0]
     geom = Geometry(L, N, dx0)
     rho_r = restrict(rho, N)
     full_M, hole_M = level_masses(rho_r, geom)
+    hole_cache, carry_cache = {}, {}
+
+    def hole_at(k, cell):
+        if cell not in hole_cache.setdefault(k, {}):
+            hole_cache[k][cell] = direct_sum_at(hole_M[k], geom.dx(k), G, np.array([cell], float))[0]
+        return hole_cache[k][cell]
+
+    def carry_at(n, cell):
+        if n == 0:
+            return 0.0
+        if (n, cell) not in carry_cache:
+            cs = [ghost_index(N, i) for i in cell]
+            p0 = tuple(int(c) for c, _ in cs)
+            p1 = tuple(int(c + sg) for c, sg in cs)
+            carry_cache[(n, cell)] = (0.75 * (hole_at(n - 1, p0) + carry_at(n - 1, p0))
+                                      + 0.25 * (hole_at(n - 1, p1) + carry_at(n - 1, p1)))
+        return carry_cache[(n, cell)]
+
+    if interp not in ("trilinear", "diagonal"):
+        raise ValueError("interp must be 'trilinear' or 'diagonal'")
     out = []
     for (n, z, y, x) in samples:
         cell = np.array([[z, y, x]], dtype=np.float64)
@@ -42,6 +68,9 @@ def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original"):
             val += direct_sum_at(rho_fine_M, geom.dx(n + 1), G, np.array(fine, float)).mean()
         else:
             raise ValueError("method must be 'original' or 'dipole'")
+        if interp == "diagonal":
+            out.append(val + carry_at(n, (int(z), int(y), int(x))))
+            continue
         for k in range(n):
             u = interp_coords(N, k, n)
             pts, wts = [], []

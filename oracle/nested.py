@@ -12,8 +12,13 @@ Readings taken where the paper is silent (each listed in the design notes):
   mass (Sect. 4, Sect. 7 "projected from the fine to the coarse grid").  The
   caller's coarse values there are ignored.
 * Cell mass M = rho(centre) * dx^3.
-* The interpolation of Fig. 6 (stripped from the source) is trilinear, from
-  level k straight to level n (no cascade through intermediate levels).
+* The interpolation of Fig. 6 (stripped from the source) has two readings:
+  interp='trilinear' (default): tensor-product linear, from level k straight
+  to level n (no cascade through intermediate levels); interp='diagonal':
+  the two-point rule of Eqs. 3-6 (3/4 of the nearest coarse centre plus 1/4
+  of its diagonal neighbour towards the fine centre), which only spans one
+  level, so the coarser holes are carried down level by level:
+  carry_n = D(carry_{n-1} + Phi^{n-1}_hole), carry_1 = D(Phi^0_hole).
 * The "reduction" of the doubled fine grid to the coarse grid (Sect. 7) is the
   mean of the 2^3 fine values in each coarse cell.
 * Eq. B.1 writes the coarser-level sum with superscript m = n; it is read as
@@ -25,6 +30,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from .acceleration import ghost_index
 from .convolution import isolated_convolution
 from .green import green_spectrum
 
@@ -127,6 +133,15 @@ def trilinear_to_level(phi_k, N, k, n):
     return out
 
 
+def diagonal_to_next(phi_k, N):
+    """The Eqs. 3-6 rule at every cell centre of level k+1 from level k: on
+    each axis the fine centre lies a quarter coarse cell from the nearest
+    coarse centre c, towards c + s; the value is 3/4 phi(c) + 1/4 phi(c + s)
+    with s the diagonal step (+-1 on every axis)."""
+    c, s = ghost_index(N, np.arange(N))
+    return 0.75 * phi_k[np.ix_(c, c, c)] + 0.25 * phi_k[np.ix_(c + s, c + s, c + s)]
+
+
 def reduce_2x(fine):
     """Mean of the 2^3 fine values in each coarse cell (the Sect. 7 reduction)."""
     n = fine.shape[0] // 2
@@ -175,7 +190,7 @@ def doubled_fine_potential(rho_fine, geom, m, G=1.0, spectrum=None):
     return isolated_convolution(Mdbl, geom.dx(m), G, spectrum)
 
 
-def solve(rho, N, dx0, G=1.0, method="original"):
+def solve(rho, N, dx0, G=1.0, method="original", interp="trilinear"):
     """Potential on every cell of every level, shape (levels, N, N, N).
 
     method='original' -- Eq. 14:
@@ -184,17 +199,28 @@ def solve(rho, N, dx0, G=1.0, method="original"):
         Phi(Omega^n) = Phi^n_hole + tilde Phi^{n+1}_dbl + sum_{k<n} tilde Phi^k_hole
                        for n below the finest level,
         Phi(Omega^L) = Phi^L + sum_{k<L} tilde Phi^k_hole on the finest.
+    interp='trilinear' takes each tilde Phi^k_hole straight from level k;
+    interp='diagonal' replaces the sum over k < n by the carried term carry_n
+    (module docstring).
     """
     rho = np.asarray(rho, dtype=np.float64)
     L = rho.shape[0]
     comp = solve_components(rho, N, dx0, G, method)
+    if interp not in ("trilinear", "diagonal"):
+        raise ValueError("interp must be 'trilinear' or 'diagonal'")
     out = np.zeros((L, N, N, N))
+    carry = None
     for n in range(L):
         if method == "original" or n == L - 1:
             phi = comp["full"][n].copy()
         else:
             phi = comp["hole"][n] + comp["dbl"][n]
-        for k in range(n):
-            phi += trilinear_to_level(comp["hole"][k], N, k, n)
+        if interp == "trilinear":
+            for k in range(n):
+                phi += trilinear_to_level(comp["hole"][k], N, k, n)
+        elif n > 0:
+            src = comp["hole"][n - 1] if carry is None else carry + comp["hole"][n - 1]
+            carry = diagonal_to_next(src, N)
+            phi += carry
         out[n] = phi
     return out

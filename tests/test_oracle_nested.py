@@ -199,3 +199,57 @@ def test_cube_symmetries(method):
     for op in ops:
         got = solve(np.ascontiguousarray(op(rho)), N, 0.125, method=method)
         assert np.max(np.abs(got - op(base))) <= 1e-13 * np.max(np.abs(base))
+
+
+@pytest.mark.parametrize("L,method", [(2, "original"), (4, "original"), (3, "dipole")])
+def test_diagonal_interp_fft_route_equals_direct_route(L, method):
+    # the carried Eqs. 3-6 interpolation: FFT convolutions + whole-level
+    # carries against direct sums + a per-cell recursion
+    N, dx0 = 8, 1.0 / 8
+    rho = wl.random_density(20 + L, L, N)
+    out = solve(rho, N, dx0, method=method, interp="diagonal")
+    rng = np.random.default_rng(1)
+    samples = [(n, *map(int, rng.integers(0, N, 3))) for n in range(L) for _ in range(3)]
+    samples += [(L - 1, 0, 0, 0), (L - 1, N - 1, 0, N - 1)]
+    ref = nested_potential_at(rho, N, dx0, samples, method=method, interp="diagonal")
+    got = np.array([out[s] for s in samples])
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(out))
+
+
+def test_diagonal_rule_linear_exact_and_quadratic_error():
+    # Eqs. 3-6 are linear interpolation along the cell diagonal at a quarter of
+    # its length: exact for linear fields, and for a quadratic with Hessian H
+    # the error is t(1-t)/2 d^T H d = (3/32) d^T H d, d = dx_k (s_x, s_y, s_z)
+    from oracle.acceleration import ghost_index
+    from oracle.nested import diagonal_to_next
+    N, dx0 = 16, 0.3
+    geo = Geometry(2, N, dx0)
+    c0, c1 = geo.centres(0), geo.centres(1)
+    Z, Y, X = np.meshgrid(c0, c0, c0, indexing="ij")
+    Zf, Yf, Xf = np.meshgrid(c1, c1, c1, indexing="ij")
+    lin = lambda x, y, z: 0.7 * x - 1.3 * y + 2.1 * z + 0.4
+    assert np.allclose(diagonal_to_next(lin(X, Y, Z), N), lin(Xf, Yf, Zf), rtol=0, atol=1e-13)
+    H = np.array([[2.0, 1.0, 0.5], [1.0, -3.0, 0.0], [0.5, 0.0, 1.5]])   # (x, y, z) order
+    q = lambda x, y, z: 0.5 * (H[0, 0] * x * x + H[1, 1] * y * y + H[2, 2] * z * z) + \
+        H[0, 1] * x * y + H[0, 2] * x * z + H[1, 2] * y * z
+    err = diagonal_to_next(q(X, Y, Z), N) - q(Xf, Yf, Zf)
+    _, s = ghost_index(N, np.arange(N))
+    Sz, Sy, Sx = np.meshgrid(s, s, s, indexing="ij")
+    d = dx0 * np.stack([Sx, Sy, Sz])
+    dHd = np.einsum("i...,ij,j...->...", d, H, d)
+    assert np.allclose(err, 3.0 / 32.0 * dHd, rtol=0, atol=1e-13)
+
+
+def test_diagonal_interp_carries_linear_holes_exactly():
+    # a potential linear in space on every hole grid is carried down any
+    # number of levels unchanged (each step is exact for linear fields)
+    from oracle.nested import diagonal_to_next
+    N, L, dx0 = 8, 4, 0.5
+    geo = Geometry(L, N, dx0)
+    f = lambda n: (lambda c: np.meshgrid(c, c, c, indexing="ij"))(geo.centres(n))
+    lin = lambda Z, Y, X: 1.1 * X + 0.3 * Y - 0.8 * Z
+    carry = None
+    for n in range(1, L):
+        hole = lin(*f(n - 1))
+        carry = diagonal_to_next(hole if carry is None else carry + hole, N)
+        assert np.allclose(carry, n * lin(*f(n)), rtol=0, atol=1e-12)
