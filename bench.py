@@ -271,6 +271,52 @@ def dipole_rates(nm, wl, torch, dev, reps=20):
     return out
 
 
+def accel_rates(nm, torch, dev, rho, w, peak, reps=20):
+    """g = -grad Phi (nm_acceleration) on the benchmarked mesh, and the solve
+    with the carried Eqs. 3-6 interpolation against the trilinear one.  The
+    acceleration kernel moves 32 bytes per cell (one double read, three
+    written), over 4 rotating phi/g sets larger than L2."""
+    L, N = w.levels, w.N
+    cells = L * N ** 3
+    p = nm.Plan(L, N, w.dx0, precision="fp64")
+    r = torch.from_numpy(rho).to(dev, torch.float64)
+    phis = [p.potential(r).clone() for _ in range(NSETS)]
+    gs = [torch.empty((L, 3, N, N, N), dtype=torch.float64, device=dev) for _ in range(NSETS)]
+    for i in range(3):
+        p.acceleration(phis[i % NSETS], gs[i % NSETS])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(reps):
+        p.acceleration(phis[i % NSETS], gs[i % NSETS])
+    b.record()
+    torch.cuda.synchronize()
+    us = a.elapsed_time(b) / reps * 1e3
+    p.close()
+    del gs
+    gbs = 32.0 * cells / (us * 1e-6) / 1e9
+    out = {"acceleration": {"workload": "contrast-%dx%d" % (L, N), "us_per_launch": us,
+                            "algorithmic_bytes": 32 * cells, "gbs": gbs, "frac": gbs / peak}}
+    diag = {}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        rr = torch.from_numpy(rho).to(dev, dt)
+        for interp in ("trilinear", "diagonal"):
+            q = nm.Plan(L, N, w.dx0, precision=prec, interp=interp)
+            n = reps if prec == "fp32" else max(2, reps // 5)
+            for i in range(3):
+                q.potential(rr, phis[i % NSETS])
+            torch.cuda.synchronize()
+            a.record()
+            for i in range(n):
+                q.potential(rr, phis[i % NSETS])
+            b.record()
+            torch.cuda.synchronize()
+            diag["%s_%s_ms" % (interp, prec)] = a.elapsed_time(b) / n
+            q.close()
+    out["interp_diagonal"] = diag
+    return out
+
+
 def max_over_ranks(torch, dist, v):
     from paper_2301_06763_gb300 import replicas
     return replicas.max_over_ranks(v, dist, device="cuda" if dist is not None else None)
@@ -374,6 +420,7 @@ def ours(args):
     kernel_table = {k: {"launches": v[0], "avg_ms": v[2] / v[0], "share": v[2] / sum(
         x[2] for x in stats.values())} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][2])}
     dip = dipole_rates(nm, wl, torch, dev) if not args.no_cpu_baseline else None
+    ext = accel_rates(nm, torch, dev, rho, w, peak) if not args.no_cpu_baseline else {}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(L, N)
@@ -402,6 +449,8 @@ def ours(args):
         "kernels": kernel_table,
         "cpu_baseline": cpu,
         "dipole": dip,
+        "acceleration": ext.get("acceleration"),
+        "interp_diagonal": ext.get("interp_diagonal"),
         "clocks": clk,
     }
     print(json.dumps(line))

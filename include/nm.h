@@ -80,7 +80,7 @@ typedef enum {
 
 enum { NM_FP64 = 0, NM_FP32 = 1 };
 enum { NM_METHOD_ORIGINAL = 0, NM_METHOD_DIPOLE_PAIR = 1 };
-enum { NM_INTERP_TRILINEAR = 0 };
+enum { NM_INTERP_TRILINEAR = 0, NM_INTERP_DIAGONAL = 1 };
 enum { NM_MAX_LEVELS = 16 };
 
 typedef struct {
@@ -95,7 +95,17 @@ typedef struct {
                         level's own potential in double.                        */
     int method;      /* NM_METHOD_ORIGINAL (Eq. 14) or NM_METHOD_DIPOLE_PAIR
                         (Eqs. 15, B.1-B.2)                                       */
-    int interp;      /* NM_INTERP_TRILINEAR (the only stencil built)            */
+    int interp;      /* How the hole potentials reach the finer levels (the
+                        stencil of Fig. 6):
+                        NM_INTERP_TRILINEAR: tensor-product linear from each
+                          level k straight to every finer level n;
+                        NM_INTERP_DIAGONAL: the two-point rule of Eqs. 3-6
+                          (3/4 of the nearest coarse value plus 1/4 of its
+                          diagonal neighbour towards the fine centre), carried
+                          one level at a time: carry_n = D(carry_{n-1} +
+                          Phi^{n-1}_hole), carry_1 = D(Phi^0_hole).  Costs
+                          L-2 extra small launches and (L-2)(N/2+2)^3 values
+                          of workspace.                                          */
 } nm_options;
 
 /* Fill `opt` with the defaults used by nm_plan: G = 1, NM_FP64, original
@@ -244,7 +254,8 @@ nm_status nm_profile_read(nm_kernel_stat* out, int max, int* count);
  * device memory belongs to another framework's allocator, and loops that
  * cannot afford cudaMalloc's implicit device-wide synchronisation.
  * It computes the same potential as nm_potential (original method, Eq. 14) for
- * the mesh described by `opt` (method must be NM_METHOD_ORIGINAL), from device
+ * the mesh described by `opt` (method must be NM_METHOD_ORIGINAL and interp
+ * NM_INTERP_TRILINEAR, else NM_EUNSUPPORTED), from device
  * `rho` to device `phi`, asynchronously on `stream`, and never allocates: all
  * scratch (spectrum, tables, work buffer, level potentials) lives in one
  * file-scope device array of NM_NOALLOC_SCRATCH_BYTES that every GPU loading

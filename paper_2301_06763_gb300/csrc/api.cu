@@ -272,6 +272,7 @@ struct nm_plan_s {
     void* work = nullptr;             // work_slots * (P/2) * P^2 complex
     void* lvl = nullptr;              // L * N^3 level potentials
     void* crop = nullptr;             // (L-1) * (N/2+2)^3 hole crops (original method)
+    void* carry = nullptr;            // (L-2) * (N/2+2)^3 carried holes (diagonal interp)
     void* dbl_work = nullptr;         // group_dbl * (2N) * (4N)^2 complex (dipole)
     void* dbl_out = nullptr;          // (L-1) * (2N)^3 (dipole)
     void* h_rho = nullptr;            // staging for nm_potential_host
@@ -300,11 +301,12 @@ void plan_free_buffers(nm_plan_t p) {
     cudaFree(p->work);
     cudaFree(p->lvl);
     cudaFree(p->crop);
+    cudaFree(p->carry);
     cudaFree(p->dbl_work);
     cudaFree(p->dbl_out);
     cudaFree(p->h_rho);
     cudaFree(p->h_phi);
-    p->restr = p->work = p->lvl = p->crop = p->dbl_work = p->dbl_out = p->h_rho = nullptr;
+    p->restr = p->work = p->lvl = p->crop = p->carry = p->dbl_work = p->dbl_out = p->h_rho = nullptr;
     p->h_phi = nullptr;
 }
 
@@ -478,7 +480,8 @@ static nm_status validate_options(const nm_options& o) {
     if (o.precision != NM_FP64 && o.precision != NM_FP32) return fail(NM_EINVAL, "bad precision %d", o.precision);
     if (o.method != NM_METHOD_ORIGINAL && o.method != NM_METHOD_DIPOLE_PAIR)
         return fail(NM_EINVAL, "bad method %d", o.method);
-    if (o.interp != NM_INTERP_TRILINEAR) return fail(NM_EUNSUPPORTED, "only trilinear interpolation is built");
+    if (o.interp != NM_INTERP_TRILINEAR && o.interp != NM_INTERP_DIAGONAL)
+        return fail(NM_EINVAL, "bad interp %d", o.interp);
     return NM_OK;
 }
 
@@ -492,6 +495,7 @@ static size_t default_footprint(const nm_options& o) {
     const size_t buf = (P / 2) * P * P * cs;
     size_t b = (L - 1) * h3 * es + (size_t)default_group(buf, npairs) * buf + L * N3 * es;
     if (!dipole) b += (L - 1) * nc * nc * nc * es;
+    if (o.interp == NM_INTERP_DIAGONAL && L > 2) b += (L - 2) * nc * nc * nc * es;
     if (dipole && L > 1) {
         const size_t buf_dbl = (2 * N) * (4 * N) * (4 * N) * cs;
         b += (size_t)default_group(buf_dbl, (int)(L / 2)) * buf_dbl + (L - 1) * 8 * N3 * es;
@@ -555,6 +559,7 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     if (e == cudaSuccess) p->work_slots = p->sched.group;
     alloc(&p->lvl, L * N3 * p->es);
     if (!p->dipole) alloc(&p->crop, (L - 1) * nc3 * p->es);
+    if (o.interp == NM_INTERP_DIAGONAL && L > 2) alloc(&p->carry, (L - 2) * nc3 * p->es);
     if (p->dipole && L > 1) {
         alloc(&p->dbl_work, (size_t)p->group_dbl * buf_dbl);
         alloc(&p->dbl_out, (L - 1) * 8 * N3 * p->es);
@@ -734,6 +739,27 @@ nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
                 a.interp_origin[n] = N / 4 - 1;
                 a.interp_extent[n] = (int)nc;
             }
+        }
+    }
+    if (p->opt.interp == NM_INTERP_DIAGONAL) {
+        // carried Eqs. 3-6 interpolation: level n reads S_{n-1} only, with
+        // S_0 = Phi^0_hole and S_n = D(S_{n-1}) + Phi^n_hole (n = 1 .. L-2)
+        a.diag = 1;
+        for (int n = 1; n + 1 < L; ++n) {
+            CarryArgs<T> c{};
+            c.prev = a.interp[n - 1];
+            c.prev_origin = a.interp_origin[n - 1];
+            c.prev_extent = a.interp_extent[n - 1];
+            c.hole = a.interp[n];
+            c.hole_origin = a.interp_origin[n];
+            c.hole_extent = a.interp_extent[n];
+            c.out = (T*)p->carry + (size_t)(n - 1) * nc3;
+            c.N = N;
+            cudaError_t e = run_carry<T>(c, s);
+            if (e != cudaSuccess) return cuda_fail(e, "carried interpolation");
+            a.interp[n] = c.out;
+            a.interp_origin[n] = N / 4 - 1;
+            a.interp_extent[n] = (int)nc;
         }
     }
     cudaError_t e = run_assemble<T>(a, s);

@@ -67,7 +67,21 @@ template <typename T> struct AssembleArgs {
     int interp_extent[16]; // its extent per axis
     double* phi;
     int levels, N;
+    int diag;              // 1: Eqs. 3-6 two-point rule from interp[n-1] only
 };
+// One step of the carried Eqs. 3-6 interpolation: on the (N/2+2)^3 cells of
+// level n from N/4-1 on, out = D(prev) + hole, prev and hole given with their
+// origin and extent on their own level.
+template <typename T> struct CarryArgs {
+    const T* prev;
+    int prev_origin, prev_extent;
+    const T* hole;
+    int hole_origin, hole_extent;
+    T* out;
+    int N;
+};
+template <typename T>
+cudaError_t run_carry(const CarryArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s);
 

@@ -235,6 +235,51 @@ template <> struct Vec4<double> {
     }
 };
 
+// Eqs. 3-6 on one axis: level-(n-1) position of level-n index i (i >= -1) is
+// (N/2 + i)/2 - 1/4 = c + s/4: nearest coarse index c, diagonal step s.
+__device__ __forceinline__ void diag_axis(int N, int i, int& c, int& s) {
+    c = (N / 2 + i) >> 1;
+    s = (i & 1) ? 1 : -1;
+}
+// The two-point rule at level-n cell (z, y, x) from a level-(n-1) field
+// stored from `o` on, `E` per axis.
+template <typename T>
+__device__ __forceinline__ T diag_value(const T* src, int o, int E, int N, int z, int y, int x) {
+    int cz, sz, cy, sy, cx, sx;
+    diag_axis(N, z, cz, sz);
+    diag_axis(N, y, cy, sy);
+    diag_axis(N, x, cx, sx);
+    const T near = src[((size_t)(cz - o) * E + (cy - o)) * E + (cx - o)];
+    const T diag = src[((size_t)(cz + sz - o) * E + (cy + sy - o)) * E + (cx + sx - o)];
+    return T(0.75) * near + T(0.25) * diag;
+}
+
+template <typename T>
+__global__ void k_carry(const __grid_constant__ CarryArgs<T> a) {
+    const int N = a.N, nc = N / 2 + 2, o = N / 4 - 1;
+    const size_t total = (size_t)nc * nc * nc;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nc) + o, y = (int)((i / nc) % nc) + o, z = (int)(i / ((size_t)nc * nc)) + o;
+        const int ho = a.hole_origin, hE = a.hole_extent;
+        const T h = a.hole[((size_t)(z - ho) * hE + (y - ho)) * hE + (x - ho)];
+        a.out[i] = diag_value<T>(a.prev, a.prev_origin, a.prev_extent, N, z, y, x) + h;
+    }
+}
+
+template <typename T>
+cudaError_t run_carry(const CarryArgs<T>& a, cudaStream_t s) {
+    ProfScope ps(sizeof(T) == 4 ? "carry_f32" : "carry_f64", 1, s);
+    const size_t nc = a.N / 2 + 2, total = nc * nc * nc;
+    size_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_carry<T><<<(int)blocks, 256, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t run_carry<float>(const CarryArgs<float>&, cudaStream_t);
+template cudaError_t run_carry<double>(const CarryArgs<double>&, cudaStream_t);
+
 // One thread per 4 consecutive cells along x (N >= 4): the z and y stencils of
 // each coarser level are shared by the 4 cells.
 template <typename T>
@@ -268,7 +313,13 @@ __global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
                 acc[c] += s * T(0.125);
             }
         }
-        for (int k = 0; k < n; ++k) {
+        if (a.diag && n > 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                acc[c] += diag_value<T>(a.interp[n - 1], a.interp_origin[n - 1], a.interp_extent[n - 1], N, z, y,
+                                        x0 + c);
+        }
+        for (int k = 0; k < (a.diag ? 0 : n); ++k) {
             const int lgr = n - k;
             int iz, iy;
             T tz, ty;
@@ -351,7 +402,13 @@ __global__ void __launch_bounds__(256) k_assemble_rows(const __grid_constant__ A
                 acc[c] += s * T(0.125);
             }
         }
-        for (int k = 0; k < n; ++k) {
+        if (a.diag && n > 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                acc[c] += diag_value<T>(a.interp[n - 1], a.interp_origin[n - 1], a.interp_extent[n - 1], N, z, y,
+                                        x0 + c);
+        }
+        for (int k = 0; k < (a.diag ? 0 : n); ++k) {
             const int lgr = n - k;
             int iz, iy, lo, hi;
             const T tz = as_t<T>(stencil_weight(N, lgr, z, iz));

@@ -19,8 +19,10 @@ LIB_PATH = os.path.join(_HERE, "libnestconv.so")
 NM_OK, NM_EINVAL, NM_ENOMEM, NM_ECUDA, NM_ETIMEOUT, NM_EUNSUPPORTED = range(6)
 FP64, FP32 = 0, 1
 ORIGINAL, DIPOLE_PAIR = 0, 1
+TRILINEAR, DIAGONAL = 0, 1
 _PREC = {"fp64": FP64, "fp32": FP32}
 _METHOD = {"original": ORIGINAL, "dipole": DIPOLE_PAIR}
+_INTERP = {"trilinear": TRILINEAR, "diagonal": DIAGONAL}
 
 
 class Options(ctypes.Structure):
@@ -118,19 +120,20 @@ def kernel_launches():
     return int(lib().nm_kernel_launches())
 
 
-def make_options(levels, N, dx0, G=1.0, precision="fp64", method="original"):
+def make_options(levels, N, dx0, G=1.0, precision="fp64", method="original", interp="trilinear"):
     o = Options()
     _check(lib().nm_default_options(int(levels), int(N), float(dx0), ctypes.byref(o)))
     o.G = float(G)
     o.precision = _PREC[precision]
     o.method = _METHOD[method]
+    o.interp = _INTERP[interp]
     return o
 
 
-def footprint_bytes(levels, N, dx0=1.0, G=1.0, precision="fp64", method="original"):
+def footprint_bytes(levels, N, dx0=1.0, G=1.0, precision="fp64", method="original", interp="trilinear"):
     """Device bytes a plan of this shape would allocate (default schedule)."""
     v = ctypes.c_size_t()
-    _check(lib().nm_footprint_bytes(ctypes.byref(make_options(levels, N, dx0, G, precision, method)),
+    _check(lib().nm_footprint_bytes(ctypes.byref(make_options(levels, N, dx0, G, precision, method, interp)),
                                     ctypes.byref(v)))
     return int(v.value)
 
@@ -172,13 +175,13 @@ def _stream_handle(stream):
 class Plan:
     """One nested mesh: ``levels`` levels of N^3 cells, coarsest cell ``dx0``."""
 
-    def __init__(self, levels, N, dx0, G=1.0, precision="fp64", method="original"):
-        o = make_options(levels, N, dx0, G, precision, method)
+    def __init__(self, levels, N, dx0, G=1.0, precision="fp64", method="original", interp="trilinear"):
+        o = make_options(levels, N, dx0, G, precision, method, interp)
         h = ctypes.c_void_p()
         _check(lib().nm_plan_ex(ctypes.byref(o), ctypes.byref(h)))
         self._h = h
         self.levels, self.N, self.dx0, self.G = int(levels), int(N), float(dx0), float(G)
-        self.precision, self.method = precision, method
+        self.precision, self.method, self.interp = precision, method, interp
 
     @property
     def handle(self):

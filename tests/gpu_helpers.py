@@ -12,12 +12,12 @@ def nm():
     return _nm
 
 
-def gpu_solve(rho, N, dx0, G=1.0, precision="fp64", method="original"):
+def gpu_solve(rho, N, dx0, G=1.0, precision="fp64", method="original", interp="trilinear"):
     import torch
     m = nm()
     L = rho.shape[0]
     dt = torch.float32 if precision == "fp32" else torch.float64
-    with m.Plan(L, N, dx0, G, precision=precision, method=method) as plan:
+    with m.Plan(L, N, dx0, G, precision=precision, method=method, interp=interp) as plan:
         r = torch.from_numpy(np.ascontiguousarray(rho)).to("cuda", dt)
         phi = plan.potential(r)
         torch.cuda.synchronize()

@@ -66,3 +66,12 @@ def test_null_arguments(lib):
     o.precision = 7
     h = ctypes.c_void_p()
     assert lib.nm_plan_ex(ctypes.byref(o), ctypes.byref(h)) == 1
+
+
+def test_noalloc_rejects_diagonal_interp_before_the_device(lib):
+    from paper_2301_06763_gb300 import nm
+    o = nm.make_options(2, 8, 0.1, interp="diagonal")
+    assert lib.nm_potential_noalloc(ctypes.byref(o), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 5
+    o.interp = 9
+    h = ctypes.c_void_p()
+    assert lib.nm_plan_ex(ctypes.byref(o), ctypes.byref(h)) == 1
