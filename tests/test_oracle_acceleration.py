@@ -122,3 +122,68 @@ def test_analytic_accelerations_are_minus_the_gradient(pt):
     h = 1e-5
     dphi = (analytic.poly_sphere(r + h, M, R) - analytic.poly_sphere(r - h, M, R)) / (2 * h)
     assert abs(float(analytic.poly_sphere_accel_radial(r, M, R)) - float(dphi)) <= 1e-6 * abs(float(dphi))
+
+
+def _face_fluxes(phi, N, n, ax, sigma, hat):
+    # coarse and fine gradients across one face of the covered block, along
+    # +sigma, from the substituted coarse field `hat`
+    a, b = N // 4, 3 * N // 4
+    cl, cov = (a - 1, a) if sigma > 0 else (b, b - 1)
+    fl, gl = (0, -1) if sigma > 0 else (N - 1, N)
+    sel = lambda i: tuple(i if t == ax else slice(a, b) for t in range(3))
+    coarse = hat[sel(cov)] - phi[n][sel(cl)]
+    from oracle.acceleration import ghost_face
+    phi_B = np.squeeze(ghost_face(hat, N, ax, gl), axis=ax)
+    fine = np.take(phi[n + 1], fl, axis=ax) - phi_B
+    h = N // 2
+    return coarse, fine.reshape(h, 2, h, 2).mean(axis=(1, 3))
+
+
+@pytest.mark.parametrize("ax,sigma", [(0, 1), (1, -1), (2, 1), (2, -1)])
+def test_method_C_matches_fluxes_across_the_interface(ax, sigma):
+    # the defining property (Appendix A, method C): after the iterations the
+    # coarse gradient across each face of the covered block equals the mean
+    # of the fine gradients across it, (V - Phi_C)/dx_n = mean (Phi_f - Phi_B)/dx_{n+1}
+    from oracle.acceleration import virtual_values
+    N, L = 16, 3
+    phi = np.random.default_rng(5).standard_normal((L, N, N, N))
+    for n in range(L - 1):
+        hat = virtual_values(phi[n], phi[n + 1], N, ax, sigma, iters=60)
+        coarse, fine = _face_fluxes(phi, N, n, ax, sigma, hat)
+        assert np.allclose(coarse / 1.0, fine / 0.5, rtol=0, atol=1e-12 * np.abs(phi).max())
+
+
+def test_method_C_iteration_converges():
+    # each sweep halves the change (the virtual value of a face cell depends on
+    # those of its four diagonal face neighbours with weight 1/8 each)
+    from oracle.acceleration import virtual_values
+    N = 16
+    phi = np.random.default_rng(6).standard_normal((2, N, N, N))
+    d = [np.abs(virtual_values(phi[0], phi[1], N, 1, 1, k + 1) - virtual_values(phi[0], phi[1], N, 1, 1, k)).max()
+         for k in (4, 8, 12)]
+    assert d[1] <= d[0] / 8 and d[2] <= d[1] / 8
+
+
+def test_method_C_exact_for_linear_and_equal_to_B_away_from_interfaces():
+    N, L, dx0 = 16, 3, 0.4
+    phi = level_field(lambda x, y, z: -0.6 * x + 1.7 * y + 0.9 * z + 2.0, L, N, dx0)
+    gC = oracle.acceleration(phi, N, dx0, coarse_side="C")
+    for comp, val in enumerate((0.6, -1.7, -0.9)):
+        assert np.allclose(gC[:, comp], val, rtol=0, atol=1e-11)
+    # a generic field: B and C differ only on the cells next to an interface
+    phi = np.random.default_rng(7).standard_normal((L, N, N, N))
+    gB = oracle.acceleration(phi, N, dx0)
+    gC = oracle.acceleration(phi, N, dx0, coarse_side="C")
+    a, b = N // 4, 3 * N // 4
+    touched = np.zeros((L, N, N, N), bool)
+    for n in range(L):
+        if n > 0:       # fine side: boundary layers
+            touched[n, [0, -1], :, :] = True
+            touched[n, :, [0, -1], :] = True
+            touched[n, :, :, [0, -1]] = True
+        if n < L - 1:   # coarse side: the layers around the covered block
+            touched[n, a - 1:b + 1, a - 1:b + 1, a - 1:b + 1] = True
+            touched[n, a:b, a:b, a:b] = False
+    diff = np.any(gB != gC, axis=1)
+    assert not np.any(diff & ~touched)
+    assert np.any(diff & touched)
