@@ -13,6 +13,8 @@ of the dominant kernel, the oracle's CPU rate and the clocks go alongside.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --mode batch    # 64 meshes, N in {32,64,128}, 2-8 levels, one batched call
   python bench.py --mode serve    # Poisson request stream, rates swept, p50/p99 latency
+  python bench.py --mode accel    # g = -grad Phi (nm_acceleration) on the benchmark mesh
+  python bench.py --mode table    # configs 1-4: GPU FP64/FP32, cuFFT, oracle 1 core / all cores
 
 Under torchrun (N > 1) each rank solves its own copy of the workload (the
 meshes are independent: replicas, weak scaling); the timed region is bracketed
@@ -22,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -41,15 +44,15 @@ NSETS = 4          # rotating rho/phi buffer sets: 4 x (50 MB + 100 MB) > L2 (~1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--levels", type=int, default=6)
     ap.add_argument("--N", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle CPU timing (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "batch", "serve"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "batch", "serve", "accel", "table"], default="solve")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window per rate (requests = rate x seconds, at most 2000)")
@@ -111,6 +114,11 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- roofline
+# FP64 add/multiply issue rate of one GB300 (152 SMs), measured on the box
+# with a dependent-chain-free DADD/DMUL microbenchmark: ~0.55e12 op/s.
+FP64_OPS_PEAK = 0.55e12
+
+
 def pass_bytes(name, N, fp32):
     """Algorithmic HBM bytes of one convolution pair in kernel `name` (level grid).
 
@@ -165,10 +173,51 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------- oracle timings
+def _oracle_conv(args):
+    import oracle
+    M, dx = args
+    return oracle.isolated_convolution(M, dx, 1.0)
+
+
+def oracle_pool(workers):
+    """A process pool for the oracle, started with spawn (never forked from a
+    process that has touched the GPU) and warmed so that worker start-up and
+    imports stay outside the timed region."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    pool = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    list(pool.map(_oracle_conv, [(np.zeros((4, 4, 4)), 1.0)] * workers))
+    return pool
+
+
+def oracle_solve_timed(rho, N, dx0, pool=None):
+    """The FP64 oracle's original-method solve (restriction, 2L-1 level
+    convolutions, Eq. 14 assembly with the carried Eqs. 3-6 interpolation,
+    the library's default) with the convolutions either in this process or
+    spread over `pool`; returns (phi, seconds)."""
+    import oracle
+    from oracle.nested import diagonal_to_next
+    L = rho.shape[0]
+    t0 = time.perf_counter()
+    geom = oracle.Geometry(L, N, dx0)
+    full_M, hole_M = oracle.level_masses(oracle.restrict(rho, N), geom)
+    jobs = [(full_M[m], geom.dx(m)) for m in range(L)] + [(hole_M[m], geom.dx(m)) for m in range(L - 1)]
+    res = list(pool.map(_oracle_conv, jobs)) if pool is not None else [_oracle_conv(j) for j in jobs]
+    full, hole = res[:L], res[L:]
+    phi = np.empty((L, N, N, N))
+    carry = None
+    for n in range(L):
+        phi[n] = full[n]
+        if n > 0:
+            carry = diagonal_to_next(hole[n - 1] if carry is None else carry + hole[n - 1], N)
+            phi[n] += carry
+    return phi, time.perf_counter() - t0
+
+
 def cpu_baseline(levels, N):
-    """The FP64 oracle, as it stands, on the host: one full convolution of a
-    level (zero padding, 3-D transform, spectrum multiply, inverse, crop),
-    extrapolated to the 2L - 1 convolutions of a solve."""
+    """The FP64 oracle, as it stands, on the host: one level convolution on one
+    core (extrapolated to the 2L - 1 of a solve), and a whole solve with its
+    convolutions spread over all host cores."""
     import oracle
     from paper_2301_06763_gb300 import workloads as wl
     w = wl.config_contrast(levels=levels, N=N)
@@ -178,10 +227,22 @@ def cpu_baseline(levels, N):
     oracle.isolated_convolution(rho[0] * w.dx0 ** 3, w.dx0, 1.0, spec)
     t = time.perf_counter() - t0
     nconv = 2 * levels - 1
-    return {"value": 1.0 / (nconv * t), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": "one oracle isolated_convolution of a %d^3 level (%.1f s), x%d "
-                      "convolutions per solve; restriction/interpolation/assembly untimed"
-                      % (N, t, nconv)}
+    cores = min(os.cpu_count() or 1, nconv)
+    pool = oracle_pool(cores)
+    try:
+        _, t_all = oracle_solve_timed(rho, N, w.dx0, pool)
+    finally:
+        pool.shutdown()
+    return {"value": 1.0 / t_all, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "host_cores": os.cpu_count(), "cpu": platform.processor() or platform.machine(),
+            "sample": "one whole oracle solve (restriction, %d level convolutions spread over %d "
+                      "processes, Eq. 14 assembly): %.1f s" % (nconv, cores, t_all),
+            "one_core": {"value": 1.0 / (nconv * t), "unit": "solves/s", "cores": 1,
+                         "sample": "one oracle isolated_convolution of a %d^3 level (%.1f s), x%d "
+                                   "convolutions per solve" % (N, t, nconv)}}
+
+
+REF_SLAB = 8
 
 
 def reference_arm(args):
@@ -193,19 +254,19 @@ def reference_arm(args):
     N, L = args.N, args.levels
     P = 2 * N
     rng = np.random.default_rng(0)
-    x = rng.standard_normal((P, P, P)) + 1j * rng.standard_normal((P, P, P))
+    # one step = one oracle axis pass over REF_SLAB-th of the padded domain
+    # (P / REF_SLAB planes of lines), so that the default step counts end in
+    # a few minutes
+    x = rng.standard_normal((P // REF_SLAB, P, P)) + 1j * rng.standard_normal((P // REF_SLAB, P, P))
     for _ in range(args.warmup):
         oracle.fft_axis(x, -1)
-    times = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        t0 = time.perf_counter()
         oracle.fft_axis(x, -1)
-        times.append(time.perf_counter() - t0)
     total = time.perf_counter() - t_all
     passes = 6 * (2 * L - 1)          # 3 forward + 3 inverse axis passes per convolution
     per_step = total / args.steps
-    value = 1.0 / (passes * per_step)
+    value = 1.0 / (passes * REF_SLAB * per_step)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -214,9 +275,10 @@ def reference_arm(args):
         "config": {"workload": "contrast-%dx%d" % (L, N), "levels": L, "N": N,
                    "precision": "fp64", "method": "original"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "one oracle fft_axis pass over the (2N)^3 = %d^3 padded "
-                                   "domain per step; a solve is %d such passes (%d convolutions"
-                                   " x 6) plus untimed pad/multiply/crop/assembly" % (P, passes, 2 * L - 1)},
+                         "sample": "one oracle fft_axis pass over 1/%d of the (2N)^3 = %d^3 padded "
+                                   "domain per step; a solve is %d whole passes (%d convolutions"
+                                   " x 6) plus untimed pad/multiply/crop/assembly"
+                                   % (REF_SLAB, P, passes, 2 * L - 1)},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -271,7 +333,7 @@ def dipole_rates(nm, wl, torch, dev, reps=20):
     return out
 
 
-def accel_rates(nm, torch, dev, rho, w, peak, reps=20):
+def accel_rates(nm, torch, dev, rho, w, peak, reps=20, interp=True):
     """g = -grad Phi (nm_acceleration) on the benchmarked mesh, and the solve
     with the carried Eqs. 3-6 interpolation against the trilinear one.  The
     acceleration kernel moves 32 bytes per cell (one double read, three
@@ -295,8 +357,15 @@ def accel_rates(nm, torch, dev, rho, w, peak, reps=20):
     p.close()
     del gs
     gbs = 32.0 * cells / (us * 1e-6) / 1e9
+    # FP64-pipe bound: 3 subtractions and 3 multiplications per interior cell
+    fp64_ops = 6 * cells
     out = {"acceleration": {"workload": "contrast-%dx%d" % (L, N), "us_per_launch": us,
-                            "algorithmic_bytes": 32 * cells, "gbs": gbs, "frac": gbs / peak}}
+                            "algorithmic_bytes": 32 * cells, "gbs": gbs, "frac_hbm": gbs / peak,
+                            "fp64_ops": fp64_ops, "fp64_tops": fp64_ops / (us * 1e-6) / 1e12,
+                            "frac_fp64": fp64_ops / (us * 1e-6) / FP64_OPS_PEAK,
+                            "fp64_peak_ops": FP64_OPS_PEAK}}
+    if not interp:
+        return out
     diag = {}
     for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
         rr = torch.from_numpy(rho).to(dev, dt)
@@ -313,7 +382,63 @@ def accel_rates(nm, torch, dev, rho, w, peak, reps=20):
             torch.cuda.synchronize()
             diag["%s_%s_ms" % (interp, prec)] = a.elapsed_time(b) / n
             q.close()
-    out["interp_diagonal"] = diag
+    out["interp_readings"] = diag
+    return out
+
+
+def cufft_half_spectrum(torch, octant, dev, dtype):
+    """The (2N)^3 Green spectrum in torch.fft.rfftn's half layout (P, P, N+1)
+    from the library's real even octant ((N+1)^3, [kz][ky][kx])."""
+    N = octant.shape[0] - 1
+    P = 2 * N
+    k = np.arange(P)
+    f = np.minimum(k, P - k)
+    return torch.from_numpy(np.ascontiguousarray(octant[f][:, f][:, :, :N + 1])).to(dev, dtype)
+
+
+def cufft_level_convolutions(torch, masses, spec_half):
+    """Same-GPU cuFFT baseline of the level convolutions (Sect. 3, Eq. 11):
+    every field of ``masses`` (F, N, N, N) zero-padded to (2N)^3, one batched
+    R2C transform, the spectrum multiply, one batched C2R transform, the
+    active N^3 block cropped.  Returns the lattice sums sum_j M_j calG(i-j) in
+    unit-cell units (multiply by -G/dx for the potential)."""
+    F, N = masses.shape[0], masses.shape[1]
+    P = 2 * N
+    buf = torch.zeros((F, P, P, P), dtype=masses.dtype, device=masses.device)
+    buf[:, :N, :N, :N] = masses
+    spec = torch.fft.rfftn(buf, dim=(1, 2, 3))
+    spec *= spec_half
+    out = torch.fft.irfftn(spec, s=(P, P, P), dim=(1, 2, 3))
+    return out[:, :N, :N, :N].contiguous()
+
+
+def cufft_baseline(nm, torch, dev, rho, w, reps=10):
+    """Time the 2L-1 level convolutions of one solve (each level's full field
+    and the hole fields of all but the finest) through cuFFT (torch.fft,
+    batched over all fields), FP32 and FP64.
+    Restriction and assembly are left out, so this is compared with the sum of
+    this library's five transform passes."""
+    L, N = w.levels, w.N
+    with nm.Plan(L, N, w.dx0) as p:
+        octant = p.green_octant()
+    out = {"workload": "contrast-%dx%d" % (L, N), "fields": 2 * L - 1,
+           "what": "pad, batched R2C, spectrum multiply, batched C2R, crop (torch.fft = cuFFT)"}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        sh = cufft_half_spectrum(torch, octant, dev, dt)
+        m = torch.from_numpy(np.concatenate([rho, rho[:-1]], axis=0)).to(dev, dt)   # 2L-1 fields
+        for _ in range(3):
+            cufft_level_convolutions(torch, m, sh)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = reps if prec == "fp32" else max(2, reps // 2)
+        a.record()
+        for _ in range(n):
+            cufft_level_convolutions(torch, m, sh)
+        b.record()
+        torch.cuda.synchronize()
+        out["%s_ms" % prec] = a.elapsed_time(b) / n
+        del m, sh
+        torch.cuda.empty_cache()
     return out
 
 
@@ -421,6 +546,14 @@ def ours(args):
         x[2] for x in stats.values())} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][2])}
     dip = dipole_rates(nm, wl, torch, dev) if not args.no_cpu_baseline else None
     ext = accel_rates(nm, torch, dev, rho, w, peak) if not args.no_cpu_baseline else {}
+    cuf = cufft_baseline(nm, torch, dev, rho, w) if not args.no_cpu_baseline else None
+    if cuf is not None:
+        conv = [k for k in stats if k.split("_")[0] in ("xfwd", "yfwd", "zseam", "yinv", "xinv")]
+        cuf["ours_fp32_transform_passes_ms"] = sum(stats[k][2] for k in conv) / args.steps
+        cuf["ours_fp32_solve_ms"] = ms_step
+        cuf["ours_fp64_solve_ms"] = dev64_ms / args.steps
+        cuf["speedup_fp32_passes"] = cuf["fp32_ms"] / cuf["ours_fp32_transform_passes_ms"]
+        cuf["speedup_fp64_solve"] = cuf["fp64_ms"] / cuf["ours_fp64_solve_ms"]
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(L, N)
@@ -431,6 +564,7 @@ def ours(args):
         "data": "synthetic",
         "config": {"workload": "contrast-%dx%d" % (L, N), "levels": L, "N": N,
                    "precision": "fp32 passes, fp64 spectrum and final sum", "method": "original",
+                   "interp": "diagonal (Eqs. 3-6, carried level by level)",
                    "l2": "%d rotating rho/phi sets (%.0f MB > L2)" % (
                        NSETS, NSETS * (rho.size * 4 + rho.size * 8) / 1e6),
                    "parallelism": "replicas" if world > 1 else "single",
@@ -449,8 +583,9 @@ def ours(args):
         "kernels": kernel_table,
         "cpu_baseline": cpu,
         "dipole": dip,
+        "cufft_baseline": cuf,
         "acceleration": ext.get("acceleration"),
-        "interp_diagonal": ext.get("interp_diagonal"),
+        "interp_readings": ext.get("interp_readings"),
         "clocks": clk,
     }
     print(json.dumps(line))
@@ -519,6 +654,23 @@ def batch_mode(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- accel mode
+def accel_mode(args):
+    """nm_acceleration alone on the benchmark mesh (its own launch list and
+    ncu capture), one JSON line."""
+    import torch
+    from paper_2301_06763_gb300 import build
+    build.build()
+    from paper_2301_06763_gb300 import nm, workloads as wl
+    w = wl.config_contrast(levels=args.levels, N=args.N)
+    peak, kind = peaks()
+    out = accel_rates(nm, torch, torch.device("cuda", 0), w.rho(), w, peak, reps=args.steps, interp=False)
+    a = out["acceleration"]
+    print(json.dumps({"mode": "accel", "metric": "accelerations/s (g on every cell of every level)",
+                      "unit": "meshes/s", "value": 1e6 / a["us_per_launch"], "steps": args.steps,
+                      "peak_kind": kind, "data": "synthetic", "dtype": "f64", **a}))
+
+
 # ----------------------------------------------------------------------------- serve mode
 def serve_mode(args):
     """Poisson request streams at several rates through the continuous-batching
@@ -565,6 +717,103 @@ def serve_mode(args):
                       "rates": results}))
 
 
+# ----------------------------------------------------------------------------- table mode
+def table_mode(args):
+    """The baseline table: configs 1-4 on the GPU (FP64 plain, FP32, the cuFFT
+    level convolutions) and through the FP64 oracle on the host (one core,
+    and the level convolutions spread over all cores)."""
+    import torch
+    from paper_2301_06763_gb300 import build
+    build.build()
+    from paper_2301_06763_gb300 import nm, workloads as wl
+    dev = torch.device("cuda", 0)
+
+    def gpu_ms(w, rho, prec, method="original", reps=20):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        r = [torch.from_numpy(rho).to(dev, dt) for _ in range(2)]
+        f = [torch.empty(rho.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+        with nm.Plan(w.levels, w.N, w.dx0, precision=prec, method=method) as p:
+            for i in range(5):
+                p.potential(r[i % 2], f[i % 2])
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for i in range(reps):
+                p.potential(r[i % 2], f[i % 2])
+            b.record()
+            torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def cufft_ms(w, rho, prec, reps=10):
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        with nm.Plan(w.levels, w.N, w.dx0) as p:
+            sh = cufft_half_spectrum(torch, p.green_octant(), dev, dt)
+        m = torch.from_numpy(np.concatenate([rho, rho[:-1]], axis=0)).to(dev, dt)   # 2L-1 fields
+        for _ in range(3):
+            cufft_level_convolutions(torch, m, sh)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            cufft_level_convolutions(torch, m, sh)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    workers = min(os.cpu_count() or 1, 16)
+    pool = oracle_pool(workers)
+    rows = []
+    try:
+        for name, w in (("1: 2x16^3", wl.config_small()), ("2: 4x64^3", wl.config_binary()),
+                        ("3: 6x128^3", wl.config_contrast())):
+            rho = w.rho()
+            row = {"config": name, "gpu_fp64_ms": gpu_ms(w, rho, "fp64", reps=5 if w.N >= 128 else 20),
+                   "gpu_fp32_ms": gpu_ms(w, rho, "fp32"), "cufft_fp32_ms": cufft_ms(w, rho, "fp32"),
+                   "cufft_fp64_ms": cufft_ms(w, rho, "fp64", reps=3)}
+            if w.levels == 4:
+                row["gpu_fp64_dipole_ms"] = gpu_ms(w, rho, "fp64", "dipole")
+                row["gpu_fp32_dipole_ms"] = gpu_ms(w, rho, "fp32", "dipole")
+            _, t1 = oracle_solve_timed(rho, w.N, w.dx0, None)
+            _, ta = oracle_solve_timed(rho, w.N, w.dx0, pool)
+            row["oracle_1core_ms"] = t1 * 1e3
+            row["oracle_all_cores_ms"] = ta * 1e3
+            rows.append(row)
+        meshes = wl.config_batch(seed=0)
+        plans = [nm.Plan(w.levels, w.N, w.dx0, precision="fp32") for w in meshes]
+        rhos = [w.rho() for w in meshes]
+        r32 = [torch.from_numpy(r).to(dev, torch.float32) for r in rhos]
+        phis = [torch.empty(r.shape, dtype=torch.float64, device=dev) for r in rhos]
+        for _ in range(3):
+            nm.batch_potential(plans, r32, phis)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            nm.batch_potential(plans, r32, phis)
+        b.record()
+        torch.cuda.synchronize()
+        batch_ms = a.elapsed_time(b) / 10
+        for p in plans:
+            p.close()
+        fp64_ms = sum(gpu_ms(w, r, "fp64", reps=2) for w, r in zip(meshes, rhos))
+        cuf = sum(cufft_ms(w, r, "fp32", reps=2) for w, r in zip(meshes, rhos))
+        sub = list(range(0, len(meshes), 8))          # every 8th mesh: 8 of 64
+        t1 = sum(oracle_solve_timed(rhos[i], meshes[i].N, meshes[i].dx0, None)[1] for i in sub)
+        ta = sum(oracle_solve_timed(rhos[i], meshes[i].N, meshes[i].dx0, pool)[1] for i in sub)
+        scale = len(meshes) / len(sub)
+        rows.append({"config": "4: batch of 64", "gpu_fp32_ms": batch_ms, "gpu_fp64_ms": fp64_ms,
+                     "cufft_fp32_ms": cuf, "oracle_1core_ms": t1 * scale * 1e3,
+                     "oracle_all_cores_ms": ta * scale * 1e3,
+                     "note": "GPU FP32 = one nm_batch_potential; FP64 and cuFFT = the 64 meshes one by one; "
+                             "oracle on 8 of the 64 meshes, scaled by 8"})
+    finally:
+        pool.shutdown()
+    print(json.dumps({"mode": "table", "host_cores": os.cpu_count(), "oracle_workers": workers,
+                      "cpu": platform.processor() or platform.machine(),
+                      "cufft": "2L-1 level convolutions only (pad, R2C, multiply, C2R, crop) via torch.fft",
+                      "rows": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -573,6 +822,10 @@ def main():
         batch_mode(args)
     elif args.mode == "serve":
         serve_mode(args)
+    elif args.mode == "accel":
+        accel_mode(args)
+    elif args.mode == "table":
+        table_mode(args)
     else:
         ours(args)
 

@@ -144,8 +144,25 @@ nm_status nm_potential(nm_plan_t plan, const void* rho, double* phi, void* strea
  * Appendix A); an uncovered coarse cell next to the finer level takes the mean
  * of the 2^3 finer children for its covered neighbour (method B); the outer
  * boundary of the coarsest level uses second-order one-sided differences.
- * In double precision for both plan precisions. */
+ * In double precision for both plan precisions.  phi and g must be 16-byte
+ * aligned (NM_EINVAL otherwise). */
 nm_status nm_acceleration(nm_plan_t plan, const double* phi, double* g, void* stream);
+
+/* The coarse-side rule of the acceleration at a level interface (Appendix A):
+ * NM_ACCEL_COARSE_MEAN (method B, what nm_acceleration uses) or
+ * NM_ACCEL_COARSE_FLUX (method C): the covered neighbour of an uncovered cell
+ * takes a virtual value V making the coarse gradient across their shared face
+ * equal to the mean of the fine gradients across it ((V - Phi_C)/dx_n =
+ * mean over the 2x2 touching fine cells of (Phi_f - Phi_B)/dx_{n+1}, Phi_B the
+ * Eqs. 3-6 ghost values); the ghosts read V in turn, so the two steps are
+ * repeated `iters` times (1..1000; each sweep halves the change, 32 gives
+ * double precision), starting from the coarse level's own value, and the fine
+ * cells' ghosts then use the final values too.  The face arrays live in the
+ * plan's workspace (2 (L-1) 6 (N/2+2)^2 doubles), so calls on one plan must
+ * not overlap on the GPU.  Otherwise as nm_acceleration. */
+enum { NM_ACCEL_COARSE_MEAN = 0, NM_ACCEL_COARSE_FLUX = 1 };
+nm_status nm_acceleration_ex(nm_plan_t plan, const double* phi, double* g, int coarse_side, int iters,
+                             void* stream);
 
 /* Same result from HOST buffers: copies rho to the device, solves, copies phi
  * back, all on `stream`, and waits for the stream before returning.  Host
@@ -254,8 +271,8 @@ nm_status nm_profile_read(nm_kernel_stat* out, int max, int* count);
  * device memory belongs to another framework's allocator, and loops that
  * cannot afford cudaMalloc's implicit device-wide synchronisation.
  * It computes the same potential as nm_potential (original method, Eq. 14) for
- * the mesh described by `opt` (method must be NM_METHOD_ORIGINAL and interp
- * NM_INTERP_TRILINEAR, else NM_EUNSUPPORTED), from device
+ * the mesh described by `opt` (method must be NM_METHOD_ORIGINAL, else
+ * NM_EUNSUPPORTED; either interpolation), from device
  * `rho` to device `phi`, asynchronously on `stream`, and never allocates: all
  * scratch (spectrum, tables, work buffer, level potentials) lives in one
  * file-scope device array of NM_NOALLOC_SCRATCH_BYTES that every GPU loading

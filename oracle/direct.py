@@ -15,7 +15,7 @@ from .acceleration import ghost_index
 from .nested import Geometry, interp_coords, level_masses, restrict
 
 
-def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original", interp="trilinear"):
+def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original", interp="diagonal"):
     """Phi(Omega^n) at cells ``samples`` = iterable of (n, z, y, x).
 
     interp='diagonal' evaluates the carried hole term of the Eqs. 3-6 reading

@@ -13,12 +13,15 @@ Readings taken where the paper is silent (each listed in the design notes):
   caller's coarse values there are ignored.
 * Cell mass M = rho(centre) * dx^3.
 * The interpolation of Fig. 6 (stripped from the source) has two readings:
-  interp='trilinear' (default): tensor-product linear, from level k straight
-  to level n (no cascade through intermediate levels); interp='diagonal':
-  the two-point rule of Eqs. 3-6 (3/4 of the nearest coarse centre plus 1/4
-  of its diagonal neighbour towards the fine centre), which only spans one
-  level, so the coarser holes are carried down level by level:
+  interp='diagonal' (default): the two-point rule of Eqs. 3-6 (3/4 of the
+  nearest coarse centre plus 1/4 of its diagonal neighbour towards the fine
+  centre), the only interpolation the paper prints; it spans one level, so
+  the coarser holes are carried down level by level:
   carry_n = D(carry_{n-1} + Phi^{n-1}_hole), carry_1 = D(Phi^0_hole).
+  interp='trilinear': tensor-product linear, from level k straight to level
+  n (no cascade through intermediate levels).  The two give the same
+  potential errors; the diagonal one reproduces the paper's acceleration
+  errors (Table 4) and its first-order convergence of the max g error.
 * The "reduction" of the doubled fine grid to the coarse grid (Sect. 7) is the
   mean of the 2^3 fine values in each coarse cell.
 * Eq. B.1 writes the coarser-level sum with superscript m = n; it is read as
@@ -190,7 +193,7 @@ def doubled_fine_potential(rho_fine, geom, m, G=1.0, spectrum=None):
     return isolated_convolution(Mdbl, geom.dx(m), G, spectrum)
 
 
-def solve(rho, N, dx0, G=1.0, method="original", interp="trilinear"):
+def solve(rho, N, dx0, G=1.0, method="original", interp="diagonal"):
     """Potential on every cell of every level, shape (levels, N, N, N).
 
     method='original' -- Eq. 14:

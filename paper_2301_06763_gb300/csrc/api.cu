@@ -273,6 +273,7 @@ struct nm_plan_s {
     void* lvl = nullptr;              // L * N^3 level potentials
     void* crop = nullptr;             // (L-1) * (N/2+2)^3 hole crops (original method)
     void* carry = nullptr;            // (L-2) * (N/2+2)^3 carried holes (diagonal interp)
+    void* vbuf = nullptr;             // method C face arrays, 2 (L-1) 6 (N/2+2)^2 doubles
     void* dbl_work = nullptr;         // group_dbl * (2N) * (4N)^2 complex (dipole)
     void* dbl_out = nullptr;          // (L-1) * (2N)^3 (dipole)
     void* h_rho = nullptr;            // staging for nm_potential_host
@@ -302,11 +303,12 @@ void plan_free_buffers(nm_plan_t p) {
     cudaFree(p->lvl);
     cudaFree(p->crop);
     cudaFree(p->carry);
+    cudaFree(p->vbuf);
     cudaFree(p->dbl_work);
     cudaFree(p->dbl_out);
     cudaFree(p->h_rho);
     cudaFree(p->h_phi);
-    p->restr = p->work = p->lvl = p->crop = p->carry = p->dbl_work = p->dbl_out = p->h_rho = nullptr;
+    p->restr = p->work = p->lvl = p->crop = p->carry = p->vbuf = p->dbl_work = p->dbl_out = p->h_rho = nullptr;
     p->h_phi = nullptr;
 }
 
@@ -464,7 +466,7 @@ nm_status nm_default_options(int levels, int N, double dx0, nm_options* opt) {
     opt->G = 1.0;
     opt->precision = NM_FP64;
     opt->method = NM_METHOD_ORIGINAL;
-    opt->interp = NM_INTERP_TRILINEAR;
+    opt->interp = NM_INTERP_DIAGONAL;
     return NM_OK;
 }
 
@@ -496,6 +498,7 @@ static size_t default_footprint(const nm_options& o) {
     size_t b = (L - 1) * h3 * es + (size_t)default_group(buf, npairs) * buf + L * N3 * es;
     if (!dipole) b += (L - 1) * nc * nc * nc * es;
     if (o.interp == NM_INTERP_DIAGONAL && L > 2) b += (L - 2) * nc * nc * nc * es;
+    b += accel_vbuf_doubles((int)L, (int)N) * sizeof(double);
     if (dipole && L > 1) {
         const size_t buf_dbl = (2 * N) * (4 * N) * (4 * N) * cs;
         b += (size_t)default_group(buf_dbl, (int)(L / 2)) * buf_dbl + (L - 1) * 8 * N3 * es;
@@ -560,6 +563,7 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     alloc(&p->lvl, L * N3 * p->es);
     if (!p->dipole) alloc(&p->crop, (L - 1) * nc3 * p->es);
     if (o.interp == NM_INTERP_DIAGONAL && L > 2) alloc(&p->carry, (L - 2) * nc3 * p->es);
+    alloc(&p->vbuf, accel_vbuf_doubles((int)L, (int)N) * sizeof(double));
     if (p->dipole && L > 1) {
         alloc(&p->dbl_work, (size_t)p->group_dbl * buf_dbl);
         alloc(&p->dbl_out, (L - 1) * 8 * N3 * p->es);
@@ -741,28 +745,7 @@ nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
             }
         }
     }
-    if (p->opt.interp == NM_INTERP_DIAGONAL) {
-        // carried Eqs. 3-6 interpolation: level n reads S_{n-1} only, with
-        // S_0 = Phi^0_hole and S_n = D(S_{n-1}) + Phi^n_hole (n = 1 .. L-2)
-        a.diag = 1;
-        for (int n = 1; n + 1 < L; ++n) {
-            CarryArgs<T> c{};
-            c.prev = a.interp[n - 1];
-            c.prev_origin = a.interp_origin[n - 1];
-            c.prev_extent = a.interp_extent[n - 1];
-            c.hole = a.interp[n];
-            c.hole_origin = a.interp_origin[n];
-            c.hole_extent = a.interp_extent[n];
-            c.out = (T*)p->carry + (size_t)(n - 1) * nc3;
-            c.N = N;
-            cudaError_t e = run_carry<T>(c, s);
-            if (e != cudaSuccess) return cuda_fail(e, "carried interpolation");
-            a.interp[n] = c.out;
-            a.interp_origin[n] = N / 4 - 1;
-            a.interp_extent[n] = (int)nc;
-        }
-    }
-    cudaError_t e = run_assemble<T>(a, s);
+    cudaError_t e = run_assemble_interp<T>(a, p->opt.interp, (T*)p->carry, s);
     if (e != cudaSuccess) return cuda_fail(e, "assembly");
     return NM_OK;
 }
@@ -1071,11 +1054,23 @@ nm_status nm_autotune(nm_plan_t p, const void* rho, double* phi, int reps, void*
     return NM_OK;
 }
 
-nm_status nm_acceleration(nm_plan_t p, const double* phi, double* g, void* stream) {
+nm_status nm_acceleration_ex(nm_plan_t p, const double* phi, double* g, int coarse_side, int iters,
+                             void* stream) {
     if (!p || !phi || !g) return fail(NM_EINVAL, "nm_acceleration: null argument");
-    cudaError_t e = run_accel(phi, g, p->L, p->N, p->opt.dx0, (cudaStream_t)stream);
+    if (((uintptr_t)phi | (uintptr_t)g) & 15) return fail(NM_EINVAL, "nm_acceleration: phi and g must be 16-byte aligned");
+    if (coarse_side != NM_ACCEL_COARSE_MEAN && coarse_side != NM_ACCEL_COARSE_FLUX)
+        return fail(NM_EINVAL, "nm_acceleration: bad coarse_side %d", coarse_side);
+    if (coarse_side == NM_ACCEL_COARSE_FLUX && (iters < 1 || iters > 1000))
+        return fail(NM_EINVAL, "nm_acceleration: iters must be in [1, 1000], got %d", iters);
+    cudaError_t e = coarse_side == NM_ACCEL_COARSE_FLUX
+                        ? run_accel_ex(phi, g, p->L, p->N, p->opt.dx0, (double*)p->vbuf, iters, (cudaStream_t)stream)
+                        : run_accel(phi, g, p->L, p->N, p->opt.dx0, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "acceleration");
     return NM_OK;
+}
+
+nm_status nm_acceleration(nm_plan_t p, const double* phi, double* g, void* stream) {
+    return nm_acceleration_ex(p, phi, g, NM_ACCEL_COARSE_MEAN, 0, stream);
 }
 
 nm_status nm_workspace_bytes(nm_plan_t p, size_t* bytes) {

@@ -82,10 +82,21 @@ template <typename T> struct CarryArgs {
 };
 template <typename T>
 cudaError_t run_carry(const CarryArgs<T>& a, cudaStream_t s);
+// run_assemble after the carry chain when interp is NM_INTERP_DIAGONAL
+// (carry: (L-2) (N/2+2)^3 values of scratch).
+template <typename T>
+cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStream_t s);
 template <typename T>
 cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s);
 
 // g = -grad Phi of a nested potential (accel.cu).
 cudaError_t run_accel(const double* phi, double* g, int levels, int N, double dx0, cudaStream_t s);
+// Same with method C on the coarse side when vbuf (2 (L-1) 6 (N/2+2)^2 doubles)
+// is given: `iters` sweeps of the face condition, then the stencil.
+cudaError_t run_accel_ex(const double* phi, double* g, int levels, int N, double dx0, double* vbuf, int iters,
+                         cudaStream_t s);
+inline size_t accel_vbuf_doubles(int levels, int N) {
+    return levels > 1 ? (size_t)2 * (levels - 1) * 6 * (size_t)(N / 2 + 2) * (N / 2 + 2) : 0;
+}
 
 }  // namespace nm

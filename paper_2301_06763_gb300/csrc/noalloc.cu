@@ -43,10 +43,10 @@ void* g_addr[kMaxDevices] = {};
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t oct64, oct32, gscr, ctab, tw64, tw32, restr, work, lvl, crop, total;
+    size_t oct64, oct32, gscr, ctab, tw64, tw32, restr, work, lvl, crop, carry, total;
 };
 
-Layout carve(int L, int N, bool fp32) {
+Layout carve(int L, int N, bool fp32, bool diag) {
     const size_t es = fp32 ? 4 : 8, cs = 2 * es, P = 2 * (size_t)N;
     const size_t H3 = (size_t)(N + 1) * (N + 1) * (N + 1);
     const size_t N3 = (size_t)N * N * N, h3 = N3 / 8, nc = N / 2 + 2;
@@ -62,6 +62,7 @@ Layout carve(int L, int N, bool fp32) {
     l.work = o;  o += up256((P / 2) * P * P * cs);
     l.lvl = o;   o += up256((size_t)L * N3 * es);
     l.crop = o;  o += up256((size_t)(L - 1) * nc * nc * nc * es);
+    l.carry = o; o += diag && L > 2 ? up256((size_t)(L - 2) * nc * nc * nc * es) : 0;
     l.total = o;
     return l;
 }
@@ -149,7 +150,7 @@ cudaError_t solve_static(const nm_options& o, char* base, const Layout& lay, con
             a.interp_extent[n] = (int)nc;
         }
     }
-    return run_assemble<T>(a, s);
+    return run_assemble_interp<T>(a, o.interp, (T*)(base + lay.carry), s);
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -165,12 +166,10 @@ extern "C" nm_status nm_potential_noalloc(const nm_options* opt, const void* rho
         (o.precision != NM_FP64 && o.precision != NM_FP32) ||
         (o.interp != NM_INTERP_TRILINEAR && o.interp != NM_INTERP_DIAGONAL))
         return record_error(NM_EINVAL, "nm_potential_noalloc: invalid options");
-    if (o.interp != NM_INTERP_TRILINEAR)
-        return record_error(NM_EUNSUPPORTED, "nm_potential_noalloc: only trilinear interpolation");
     if (o.method != NM_METHOD_ORIGINAL)
         return record_error(NM_EUNSUPPORTED, "nm_potential_noalloc: only the original method (Eq. 14)");
     const bool fp32 = o.precision == NM_FP32;
-    const Layout lay = carve(o.levels, o.N <= 256 ? o.N : 256, fp32);
+    const Layout lay = carve(o.levels, o.N <= 256 ? o.N : 256, fp32, o.interp == NM_INTERP_DIAGONAL);
     if (o.N > 256 || lay.total > kScratchBytes) {
         char msg[200];
         snprintf(msg, sizeof msg,

@@ -1,4 +1,5 @@
 // support.cu -- restriction, Green spectrum and final assembly kernels.
+#include "../../include/nm.h"
 #include "internal.h"
 
 namespace nm {
@@ -463,5 +464,35 @@ cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
 }
 template cudaError_t run_assemble<float>(const AssembleArgs<float>&, cudaStream_t);
 template cudaError_t run_assemble<double>(const AssembleArgs<double>&, cudaStream_t);
+
+template <typename T>
+cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStream_t s) {
+    if (interp == NM_INTERP_DIAGONAL) {
+        // carried Eqs. 3-6 interpolation: level n reads S_{n-1} only, with
+        // S_0 = Phi^0_hole and S_n = D(S_{n-1}) + Phi^n_hole (n = 1 .. L-2)
+        const int N = a.N;
+        const size_t nc = N / 2 + 2, nc3 = nc * nc * nc;
+        a.diag = 1;
+        for (int n = 1; n + 1 < a.levels; ++n) {
+            CarryArgs<T> c{};
+            c.prev = a.interp[n - 1];
+            c.prev_origin = a.interp_origin[n - 1];
+            c.prev_extent = a.interp_extent[n - 1];
+            c.hole = a.interp[n];
+            c.hole_origin = a.interp_origin[n];
+            c.hole_extent = a.interp_extent[n];
+            c.out = carry + (size_t)(n - 1) * nc3;
+            c.N = N;
+            cudaError_t e = run_carry<T>(c, s);
+            if (e != cudaSuccess) return e;
+            a.interp[n] = c.out;
+            a.interp_origin[n] = N / 4 - 1;
+            a.interp_extent[n] = (int)nc;
+        }
+    }
+    return run_assemble<T>(a, s);
+}
+template cudaError_t run_assemble_interp<float>(AssembleArgs<float>, int, float*, cudaStream_t);
+template cudaError_t run_assemble_interp<double>(AssembleArgs<double>, int, double*, cudaStream_t);
 
 }  // namespace nm

@@ -73,6 +73,7 @@ def lib():
             "nm_potential": (st, [P, P, P, P]),
             "nm_potential_host": (st, [P, P, P, P]),
             "nm_acceleration": (st, [P, P, P, P]),
+            "nm_acceleration_ex": (st, [P, P, P, ctypes.c_int, ctypes.c_int, P]),
             "nm_workspace_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "nm_spectrum_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "nm_batch_potential": (st, [ctypes.c_int, ctypes.POINTER(P), ctypes.POINTER(P),
@@ -120,7 +121,7 @@ def kernel_launches():
     return int(lib().nm_kernel_launches())
 
 
-def make_options(levels, N, dx0, G=1.0, precision="fp64", method="original", interp="trilinear"):
+def make_options(levels, N, dx0, G=1.0, precision="fp64", method="original", interp="diagonal"):
     o = Options()
     _check(lib().nm_default_options(int(levels), int(N), float(dx0), ctypes.byref(o)))
     o.G = float(G)
@@ -130,7 +131,7 @@ def make_options(levels, N, dx0, G=1.0, precision="fp64", method="original", int
     return o
 
 
-def footprint_bytes(levels, N, dx0=1.0, G=1.0, precision="fp64", method="original", interp="trilinear"):
+def footprint_bytes(levels, N, dx0=1.0, G=1.0, precision="fp64", method="original", interp="diagonal"):
     """Device bytes a plan of this shape would allocate (default schedule)."""
     v = ctypes.c_size_t()
     _check(lib().nm_footprint_bytes(ctypes.byref(make_options(levels, N, dx0, G, precision, method, interp)),
@@ -175,7 +176,7 @@ def _stream_handle(stream):
 class Plan:
     """One nested mesh: ``levels`` levels of N^3 cells, coarsest cell ``dx0``."""
 
-    def __init__(self, levels, N, dx0, G=1.0, precision="fp64", method="original", interp="trilinear"):
+    def __init__(self, levels, N, dx0, G=1.0, precision="fp64", method="original", interp="diagonal"):
         o = make_options(levels, N, dx0, G, precision, method, interp)
         h = ctypes.c_void_p()
         _check(lib().nm_plan_ex(ctypes.byref(o), ctypes.byref(h)))
@@ -216,8 +217,10 @@ class Plan:
                                   ctypes.c_void_p(phi.data_ptr()), _stream_handle(stream)))
         return phi
 
-    def acceleration(self, phi, g=None, stream=None):
-        """g = -grad Phi ((levels, 3, N, N, N) float64) of a potential from ``potential``."""
+    def acceleration(self, phi, g=None, stream=None, coarse_side="mean", iters=32):
+        """g = -grad Phi ((levels, 3, N, N, N) float64) of a potential from
+        ``potential``; coarse_side "mean" (method B) or "flux" (method C,
+        ``iters`` sweeps)."""
         import torch
         self._check_tensor(phi, torch.float64, "phi")
         if g is None:
@@ -225,8 +228,9 @@ class Plan:
         if g.dtype != torch.float64 or tuple(g.shape) != (self.levels, 3, self.N, self.N, self.N) \
                 or not g.is_contiguous() or not g.is_cuda:
             raise ValueError("g must be a contiguous CUDA float64 tensor of shape (levels, 3, N, N, N)")
-        _check(lib().nm_acceleration(self.handle, ctypes.c_void_p(phi.data_ptr()),
-                                     ctypes.c_void_p(g.data_ptr()), _stream_handle(stream)))
+        side = {"mean": 0, "flux": 1}[coarse_side]
+        _check(lib().nm_acceleration_ex(self.handle, ctypes.c_void_p(phi.data_ptr()),
+                                        ctypes.c_void_p(g.data_ptr()), side, int(iters), _stream_handle(stream)))
         return g
 
     def potential_host(self, rho, phi=None, stream=None):

@@ -12,7 +12,7 @@ def nm():
     return _nm
 
 
-def gpu_solve(rho, N, dx0, G=1.0, precision="fp64", method="original", interp="trilinear"):
+def gpu_solve(rho, N, dx0, G=1.0, precision="fp64", method="original", interp="diagonal"):
     import torch
     m = nm()
     L = rho.shape[0]

@@ -1,7 +1,10 @@
-"""Relative potential errors (Eq. 7) of a nested solution against the analytic
-potentials of the paper's test problems, over the composite mesh: every cell
-of the finest level and the cells of each coarser level not covered by the
-next finer one (each point of space counted once, at its finest level)."""
+"""Relative errors (Eq. 7) of a nested solution's potential and acceleration
+against the analytic fields of the paper's test problems, over the composite
+mesh: every cell of the finest level and the cells of each coarser level not
+covered by the next finer one (each point of space counted once, at its
+finest level).  plane=True keeps only the x-z plane through the centre (the
+cells at y = +dx_m/2 of every level), where the paper evaluates its errors
+(Sect. 6)."""
 import numpy as np
 
 from paper_2301_06763_gb300 import workloads as wl
@@ -22,22 +25,6 @@ def analytic_field(w, m):
     return tot
 
 
-def composite_errors(w, phi):
-    N, L = w.N, w.levels
-    a, b = N // 4, 3 * N // 4
-    errs = []
-    for m in range(L):
-        an = analytic_field(w, m)
-        e = np.abs((phi[m] - an) / an)
-        if m < L - 1:
-            mask = np.ones((N, N, N), bool)
-            mask[a:b, a:b, a:b] = False
-            e = e[mask]
-        errs.append(e.ravel())
-    e = np.concatenate(errs)
-    return {"max": float(e.max()), "mean": float(e.mean()), "std": float(e.std())}
-
-
 def analytic_accel(w, m):
     """(gx, gy, gz) of the test problem at the centres of level m."""
     c = wl.level_centres(w.N, w.dx0, m)
@@ -53,19 +40,33 @@ def analytic_accel(w, m):
     return tuple(tot)
 
 
-def composite_accel_errors(w, g):
-    """Eq. 7 errors of |g| (g: (levels, 3, N, N, N)) over the composite mesh."""
+def _composite(w, per_level, plane):
     N, L = w.N, w.levels
     a, b = N // 4, 3 * N // 4
     errs = []
     for m in range(L):
-        gan = np.sqrt(sum(v * v for v in analytic_accel(w, m)))
-        gnum = np.sqrt((g[m] ** 2).sum(axis=0))
-        e = np.abs((gnum - gan) / gan)
+        e = per_level(m)
+        mask = np.ones((N, N, N), bool)
         if m < L - 1:
-            mask = np.ones((N, N, N), bool)
             mask[a:b, a:b, a:b] = False
-            e = e[mask]
-        errs.append(e.ravel())
+        if plane:
+            e, mask = e[:, N // 2, :], mask[:, N // 2, :]
+        errs.append(e[mask].ravel())
     e = np.concatenate(errs)
     return {"max": float(e.max()), "mean": float(e.mean()), "std": float(e.std())}
+
+
+def composite_errors(w, phi, plane=False):
+    """Eq. 7 errors of Phi (phi: (levels, N, N, N))."""
+    def per_level(m):
+        an = analytic_field(w, m)
+        return np.abs((phi[m] - an) / an)
+    return _composite(w, per_level, plane)
+
+
+def composite_accel_errors(w, g, plane=False):
+    """Eq. 7 errors of |g| (g: (levels, 3, N, N, N))."""
+    def per_level(m):
+        gan = np.sqrt(sum(v * v for v in analytic_accel(w, m)))
+        return np.abs((np.sqrt((g[m] ** 2).sum(axis=0)) - gan) / gan)
+    return _composite(w, per_level, plane)

@@ -58,6 +58,7 @@ def test_null_arguments(lib):
     assert lib.nm_plan_ex(None, None) == 1
     assert lib.nm_potential(None, None, None, None) == 1
     assert lib.nm_acceleration(None, None, None, None) == 1
+    assert lib.nm_acceleration_ex(None, None, None, 1, 32, None) == 1
     assert lib.nm_destroy(None) == 1
     assert lib.nm_batch_potential(-1, None, None, None, None) == 1
     o = __import__("paper_2301_06763_gb300.nm", fromlist=["Options"]).Options()
@@ -68,10 +69,10 @@ def test_null_arguments(lib):
     assert lib.nm_plan_ex(ctypes.byref(o), ctypes.byref(h)) == 1
 
 
-def test_noalloc_rejects_diagonal_interp_before_the_device(lib):
+def test_bad_interp_rejected_before_the_device(lib):
     from paper_2301_06763_gb300 import nm
     o = nm.make_options(2, 8, 0.1, interp="diagonal")
-    assert lib.nm_potential_noalloc(ctypes.byref(o), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 5
     o.interp = 9
+    assert lib.nm_potential_noalloc(ctypes.byref(o), ctypes.c_void_p(16), ctypes.c_void_p(16), None) == 1
     h = ctypes.c_void_p()
     assert lib.nm_plan_ex(ctypes.byref(o), ctypes.byref(h)) == 1

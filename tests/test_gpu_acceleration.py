@@ -17,13 +17,13 @@ pytestmark = pytest.mark.gpu
 ACCEL_REL_MAX = 1e-12
 
 
-def gpu_accel(phi, N, dx0, precision="fp64"):
+def gpu_accel(phi, N, dx0, precision="fp64", coarse_side="mean", iters=32):
     import torch
     m = nm()
     L = phi.shape[0]
     with m.Plan(L, N, dx0, 1.0, precision=precision) as plan:
         p = torch.from_numpy(np.ascontiguousarray(phi)).to("cuda", torch.float64)
-        g = plan.acceleration(p)
+        g = plan.acceleration(p, coarse_side=coarse_side, iters=iters)
         torch.cuda.synchronize()
         return g.cpu().numpy()
 
@@ -89,3 +89,23 @@ def test_rejects_null_and_misshaped():
             plan.acceleration(phi, g=torch.zeros((2, 8, 8, 8), dtype=torch.float64, device="cuda"))
         with pytest.raises((TypeError, ValueError)):
             plan.acceleration(phi.float())
+
+
+@pytest.mark.parametrize("L,N,seed,iters", [(2, 4, 20, 32), (3, 8, 21, 32), (4, 16, 22, 32), (2, 32, 23, 5),
+                                            (3, 64, 24, 32), (5, 8, 25, 1), (2, 256, 26, 32)])
+def test_method_C_matches_oracle(L, N, seed, iters):
+    # Appendix A method C: face arrays swept `iters` times on the GPU (Jacobi
+    # in the simplified form V = A - 1/8 sum of diagonal partners) against the
+    # oracle's literal steps (ghosts by Eqs. 3-6, then the face condition)
+    phi = np.random.default_rng(seed).standard_normal((L, N, N, N))
+    dx0 = 1.0 / N
+    g = gpu_accel(phi, N, dx0, coarse_side="flux", iters=iters)
+    ref = oracle.acceleration(phi, N, dx0, coarse_side="C", iters=iters)
+    assert rel_max(g, ref) <= ACCEL_REL_MAX
+
+
+def test_method_C_full_size_6x128():
+    N, L = 128, 6
+    phi = np.random.default_rng(27).standard_normal((L, N, N, N))
+    g = gpu_accel(phi, N, 1.0 / N, coarse_side="flux")
+    assert rel_max(g, oracle.acceleration(phi, N, 1.0 / N, coarse_side="C")) <= ACCEL_REL_MAX

@@ -1,13 +1,13 @@
-"""The paper's printed accuracy (Table 3, convolution method, four nested grids
-of 128^3): the CUDA FP64 and FP32 paths on the paper's two test problems,
-against their analytic potentials (Eq. 7 errors over the composite mesh).
+"""The paper's printed potential accuracy (Table 3, convolution method, four
+nested grids of 128^3): the CUDA FP64 and FP32 paths on the paper's two test
+problems against their analytic potentials, Eq. 7 errors over the composite
+mesh on the x-z plane through the centre (where Sect. 6 evaluates them).
 
-The paper does not state over which cells it averages, so max and mean are
-held to 25 % and 30 % of the printed values and the spread to a factor 2.5
-(measured on GB300: ellipsoid 0.047 / 0.0034 / 0.0021 %, binary
-0.84 / 0.40 / 0.049 %)."""
-import os
-
+Measured on GB300 (printed values in brackets): ellipsoid 0.0442 (0.045) /
+0.0035 (0.004) / 0.0036 (0.004) %, binary 0.839 (0.85) / 0.394 (0.43) /
+0.0655 (0.078) % for max / mean / spread; every number is held to 20 % of the
+printed one.  Over the whole volume the numbers barely move (ellipsoid 0.047 /
+0.0034 / 0.0026 %, binary 0.84 / 0.40 / 0.049 %)."""
 import numpy as np
 import pytest
 
@@ -27,7 +27,8 @@ def test_reproduces_table3(problem, precision):
     rho = w.rho()
     phi = gpu_solve(rho if precision == "fp64" else rho.astype(np.float32), w.N, w.dx0,
                     precision=precision)
-    e = {k: 100.0 * v for k, v in composite_errors(w, phi).items()}
-    assert abs(e["max"] - g[problem + "_max"]) <= 0.25 * g[problem + "_max"]
-    assert abs(e["mean"] - g[problem + "_mean"]) <= 0.30 * g[problem + "_mean"]
-    assert g[problem + "_std"] / 2.5 <= e["std"] <= 2.5 * g[problem + "_std"]
+    e = {k: 100.0 * v for k, v in composite_errors(w, phi, plane=True).items()}
+    print(problem, precision, e)
+    for k in ("max", "mean", "std"):
+        ref = g[problem + "_" + k]
+        assert abs(e[k] - ref) <= 0.2 * ref, (k, e[k], ref)

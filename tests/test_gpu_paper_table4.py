@@ -1,16 +1,17 @@
 """The paper's printed acceleration errors (Table 4, convolution method, four
-nested grids of 128^3): CUDA potential with the carried Eqs. 3-6 interpolation
-(NM_INTERP_DIAGONAL), then the CUDA acceleration, against the closed-form g of
-the two test problems (Eq. 7 errors of |g| over the composite mesh).
+nested grids of 128^3): the CUDA potential (default, carried Eqs. 3-6
+interpolation) and the CUDA acceleration against the closed-form g of the two
+test problems, Eq. 7 errors of |g| over the composite mesh on the x-z plane
+through the centre (where Sect. 6 evaluates them).
 
-Under this reading the binary star lands on the printed max and mean (oracle
-at the same size: 9.40 % and 0.383 %); its spread is lower than printed
-(0.18 vs 0.29 %).  The ellipsoid's errors are above the printed ones
-(oracle: 2.34 / 0.104 / 0.193 % against 1.74 / 0.05 / 0.12 %): its mean is
-dominated by the hole-potential interpolation error, whose size depends on the
-stencil of Fig. 6, which the source does not carry.  The bounds below hold
-each number to what this reading gives, around the printed value."""
-import numpy as np
+Measured on GB300 (printed values in brackets), max / mean / spread:
+ellipsoid 1.740 (1.74) / 0.087 (0.05) / 0.151 (0.12) %, binary 9.402 (9.4) /
+0.408 (0.38) / 0.295 (0.29) %.  Both maxima and the binary's mean and spread
+are held to 5-10 % of the printed values; the ellipsoid's mean and spread sit
+above them (its mean is set by the interpolated hole potentials near the
+centre, where |g| vanishes) and are held to their measured values within
+20 %.  With the tensor-product (trilinear) reading of Fig. 6 the maxima would
+be 7.2 % and 12.9 %."""
 import pytest
 
 from paper_2301_06763_gb300 import workloads as wl
@@ -22,8 +23,8 @@ pytestmark = pytest.mark.gpu
 
 # (low, high) as factors of the printed value
 BOUNDS = {
-    "binary_max": (0.9, 1.1), "binary_mean": (0.9, 1.1), "binary_std": (0.5, 1.1),
-    "ellipsoid_max": (0.9, 1.5), "ellipsoid_mean": (1.0, 2.5), "ellipsoid_std": (1.0, 2.0),
+    "binary_max": (0.95, 1.05), "binary_mean": (0.9, 1.15), "binary_std": (0.9, 1.1),
+    "ellipsoid_max": (0.95, 1.05), "ellipsoid_mean": (1.4, 2.1), "ellipsoid_std": (1.0, 1.5),
 }
 
 
@@ -32,12 +33,12 @@ def gpu_accel_errors(w, precision):
     m = nm()
     rho = w.rho()
     dt = torch.float32 if precision == "fp32" else torch.float64
-    with m.Plan(w.levels, w.N, w.dx0, 1.0, precision=precision, interp="diagonal") as plan:
+    with m.Plan(w.levels, w.N, w.dx0, 1.0, precision=precision) as plan:
         phi = plan.potential(torch.from_numpy(rho).to("cuda", dt))
         g = plan.acceleration(phi)
         torch.cuda.synchronize()
         g = g.cpu().numpy()
-    return {k: 100.0 * v for k, v in composite_accel_errors(w, g).items()}
+    return {k: 100.0 * v for k, v in composite_accel_errors(w, g, plane=True).items()}
 
 
 @pytest.mark.parametrize("problem", ["ellipsoid", "binary"])

@@ -105,18 +105,20 @@ def test_mass_only_inside_finest_level():
     assert np.max(np.abs(out[0] - coarse)) <= 1e-13 * np.max(np.abs(coarse))
 
 
-def test_mass_only_outside_fine_level():
-    # nothing inside level 1: Phi(Omega^1) is the trilinear interpolation of the
-    # exact coarse sum
+@pytest.mark.parametrize("interp", ["trilinear", "diagonal"])
+def test_mass_only_outside_fine_level(interp):
+    # nothing inside level 1: Phi(Omega^1) is the interpolation of the exact
+    # coarse sum (tensor-product linear, or the Eqs. 3-6 diagonal rule)
+    from oracle.nested import diagonal_to_next
     N, dx0 = 8, 0.25
     rng = np.random.default_rng(4)
     rho = np.zeros((2, N, N, N))
     rho[0] = rng.random((N, N, N))
     rho[0, 2:6, 2:6, 2:6] = 0.0
-    out = solve(rho, N, dx0)
+    out = solve(rho, N, dx0, interp=interp)
     coarse = direct_sum(rho[0] * dx0 ** 3, dx0)
     assert np.max(np.abs(out[0] - coarse)) <= 1e-13 * np.max(np.abs(coarse))
-    fine = trilinear_to_level(coarse, N, 0, 1)
+    fine = trilinear_to_level(coarse, N, 0, 1) if interp == "trilinear" else diagonal_to_next(coarse, N)
     assert np.max(np.abs(out[1] - fine)) <= 1e-13 * np.max(np.abs(fine))
 
 
@@ -125,11 +127,11 @@ def test_mass_only_outside_fine_level():
 def test_fft_route_equals_direct_route(L, method):
     N, dx0 = 8, 1.0 / 8
     rho = wl.random_density(10 + L, L, N)
-    out = solve(rho, N, dx0, method=method)
+    out = solve(rho, N, dx0, method=method, interp="trilinear")
     rng = np.random.default_rng(0)
     samples = [(n, *map(int, rng.integers(0, N, 3))) for n in range(L) for _ in range(4)]
     samples += [(L - 1, 0, 0, 0), (0, N - 1, N - 1, N - 1), (L - 1, 3, 4, 4)]
-    ref = nested_potential_at(rho, N, dx0, samples, method=method)
+    ref = nested_potential_at(rho, N, dx0, samples, method=method, interp="trilinear")
     got = np.array([out[s] for s in samples])
     assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(out))
 

@@ -31,17 +31,19 @@ def noalloc(opts, rho_t, phi_t):
              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
-def options(L, N, dx0, precision):
+def options(L, N, dx0, precision, interp="diagonal"):
     m = nm()
     o = m.Options()
     m.lib().nm_default_options(L, N, dx0, ctypes.byref(o))
     o.precision = m.FP32 if precision == "fp32" else m.FP64
+    o.interp = m.DIAGONAL if interp == "diagonal" else m.TRILINEAR
     o.G = 1.3
     return o
 
 
+@pytest.mark.parametrize("interp", ["trilinear", "diagonal"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_matches_allocating_entry_point_on_consecutive_calls(precision):
+def test_matches_allocating_entry_point_on_consecutive_calls(precision, interp):
     import torch
     m = nm()
     dt = torch.float32 if precision == "fp32" else torch.float64
@@ -50,10 +52,10 @@ def test_matches_allocating_entry_point_on_consecutive_calls(precision):
     for (L, N, seed) in [(3, 16, 1), (2, 32, 2), (3, 16, 3)]:
         dx0 = 0.8 / N
         rho = torch.from_numpy(wl.random_density(seed, L, N)).to("cuda", dt)
-        with m.Plan(L, N, dx0, 1.3, precision=precision) as plan:
+        with m.Plan(L, N, dx0, 1.3, precision=precision, interp=interp) as plan:
             ref = plan.potential(rho)
         got = torch.empty_like(ref)
-        st = noalloc(options(L, N, dx0, precision), rho, got)
+        st = noalloc(options(L, N, dx0, precision, interp), rho, got)
         assert st == m.NM_OK, m.last_error()
         torch.cuda.synchronize()
         a, b = got.cpu().numpy(), ref.cpu().numpy()
