@@ -52,7 +52,24 @@ def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original", interp="
         cell = np.array([[z, y, x]], dtype=np.float64)
         if method == "original" or n == L - 1:
             val = direct_sum_at(full_M[n], geom.dx(n), G, cell)[0]
-        elif method == "dipole":
+        elif method in ("dipole3", "dipole3_ds") and n < L - 2:
+            # Eqs. B.3 and B.6: own hole grid, level n+1's ring (level n+2's
+            # region emptied) on its doubled grid reduced by 2^3, and level
+            # n+2 on its quadrupled grid reduced by 4^3, or summed directly
+            # at the level-n centre
+            val = direct_sum_at(hole_M[n], geom.dx(n), G, cell)[0]
+            sub2 = [[2 * z + dz - N // 2, 2 * y + dy - N // 2, 2 * x + dx - N // 2]
+                    for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)]
+            val += direct_sum_at(hole_M[n + 1], geom.dx(n + 1), G, np.array(sub2, float)).mean()
+            M2 = rho_r[n + 2] * geom.dx(n + 2) ** 3
+            if method == "dipole3":
+                sub4 = [[4 * z + dz - 3 * N // 2, 4 * y + dy - 3 * N // 2, 4 * x + dx - 3 * N // 2]
+                        for dz in range(4) for dy in range(4) for dx in range(4)]
+                val += direct_sum_at(M2, geom.dx(n + 2), G, np.array(sub4, float)).mean()
+            else:
+                centre = [[4 * v + 1.5 - 1.5 * N for v in (z, y, x)]]
+                val += direct_sum_at(M2, geom.dx(n + 2), G, np.array(centre, float))[0]
+        elif method in ("dipole", "dipole3", "dipole3_ds"):
             val = direct_sum_at(hole_M[n], geom.dx(n), G, cell)[0]
             # doubled fine grid of level n+1: 2N cells spanning level n, fine
             # block at [N/2, 3N/2).  The 2^3 fine cells inside coarse cell
@@ -67,7 +84,7 @@ def nested_potential_at(rho, N, dx0, samples, G=1.0, method="original", interp="
             rho_fine_M = rho_r[n + 1] * geom.dx(n + 1) ** 3
             val += direct_sum_at(rho_fine_M, geom.dx(n + 1), G, np.array(fine, float)).mean()
         else:
-            raise ValueError("method must be 'original' or 'dipole'")
+            raise ValueError("method must be 'original', 'dipole', 'dipole3' or 'dipole3_ds'")
         if interp == "diagonal":
             out.append(val + carry_at(n, (int(z), int(y), int(x))))
             continue

@@ -193,6 +193,73 @@ def doubled_fine_potential(rho_fine, geom, m, G=1.0, spectrum=None):
     return isolated_convolution(Mdbl, geom.dx(m), G, spectrum)
 
 
+def doubled_hole_potential(rho_fine, geom, m, G=1.0, spectrum=None):
+    """Phi^m_dbl,hole of Appendix B (Fig. App0): as `doubled_fine_potential`,
+    with the cells of level m covered by level m+1 emptied, so that the
+    finer levels' mass is not counted twice."""
+    N = geom.N
+    a, b = geom.covered
+    M = rho_fine.copy()
+    M[a:b, a:b, a:b] = 0.0
+    return doubled_fine_potential(M, geom, m, G, spectrum)
+
+
+def quadrupled_potential(rho_fine, geom, m, G=1.0, spectrum=None):
+    """Phi^m_qdp of Appendix B (Fig. App0): level m's mass on a grid of
+    level-m cells extended to the physical size of level m-2 (4N cells per
+    axis); the level-m block sits in cells [3N/2, 5N/2), the rest carries zero
+    mass.  Returns the potential on all (4N)^3 cells."""
+    N = geom.N
+    Mq = np.zeros((4 * N, 4 * N, 4 * N))
+    a, b = 3 * N // 2, 5 * N // 2
+    Mq[a:b, a:b, a:b] = rho_fine * geom.dx(m) ** 3
+    return isolated_convolution(Mq, geom.dx(m), G, spectrum)
+
+
+def reduce_4x(fine):
+    """Mean of the 4^3 fine values in each coarse cell (Phi_qdp reduced two
+    levels down)."""
+    n = fine.shape[0] // 4
+    return fine.reshape(n, 4, n, 4, n, 4).mean(axis=(1, 3, 5))
+
+
+def direct_two_down(rho_fine, geom, m, G=1.0):
+    """Eq. B.6: the potential of level m's mass at the cell centres of level
+    m-2 by direct summation of the inverse distance between the centres,
+    -G sum_j M_j / |x_i - x_j| (the centres never coincide).  O(N^6)."""
+    N = geom.N
+    cf, cc = geom.centres(m), geom.centres(m - 2)
+    M = (rho_fine * geom.dx(m) ** 3).ravel()
+    Z, Y, X = np.meshgrid(cf, cf, cf, indexing="ij")
+    src = np.stack([Z.ravel(), Y.ravel(), X.ravel()], axis=1)
+    nz = M != 0.0
+    src, M = src[nz], M[nz]
+    Zc, Yc, Xc = np.meshgrid(cc, cc, cc, indexing="ij")
+    tgt = np.stack([Zc.ravel(), Yc.ravel(), Xc.ravel()], axis=1)
+    out = np.empty(len(tgt))
+    for i0 in range(0, len(tgt), 256):
+        d = tgt[i0:i0 + 256, None, :] - src[None, :, :]
+        out[i0:i0 + 256] = -G * (M[None, :] / np.sqrt((d * d).sum(axis=-1))).sum(axis=1)
+    return out.reshape(N, N, N)
+
+
+def triple_terms(rho_r, geom, G, quadrupled=True):
+    """The two finer-level terms of Eq. B.3 for every level n < L-2:
+    reduce_2x(Phi^{n+1}_dbl,hole) and either reduce_4x(Phi^{n+2}_qdp) or,
+    with quadrupled=False, the direct sum of Eq. B.6 from level n+2."""
+    L, N = geom.levels, geom.N
+    spec2 = green_spectrum(2 * N)
+    spec4 = green_spectrum(4 * N) if quadrupled else None
+    dbl, two = [None] * L, [None] * L
+    for n in range(L - 2):
+        dbl[n] = reduce_2x(doubled_hole_potential(rho_r[n + 1], geom, n + 1, G, spec2))
+        if quadrupled:
+            two[n] = reduce_4x(quadrupled_potential(rho_r[n + 2], geom, n + 2, G, spec4))
+        else:
+            two[n] = direct_two_down(rho_r[n + 2], geom, n + 2, G)
+    return dbl, two
+
+
 def solve(rho, N, dx0, G=1.0, method="original", interp="diagonal"):
     """Potential on every cell of every level, shape (levels, N, N, N).
 
@@ -202,13 +269,23 @@ def solve(rho, N, dx0, G=1.0, method="original", interp="diagonal"):
         Phi(Omega^n) = Phi^n_hole + tilde Phi^{n+1}_dbl + sum_{k<n} tilde Phi^k_hole
                        for n below the finest level,
         Phi(Omega^L) = Phi^L + sum_{k<L} tilde Phi^k_hole on the finest.
+    method='dipole3'  -- dipole moments across three neighbouring levels,
+        Eqs. B.3-B.5: for n < L-2 (0-based)
+        Phi(Omega^n) = Phi^n_hole + tilde Phi^{n+1}_dbl,hole + tilde Phi^{n+2}_qdp
+                       + sum_{k<n} tilde Phi^k_hole,
+        level L-2 as in the pairwise method, the finest as in Eq. 14.
+    method='dipole3_ds' -- the same with tilde Phi^{n+2}_qdp replaced by the
+        direct sum of Eq. B.6.
     interp='trilinear' takes each tilde Phi^k_hole straight from level k;
     interp='diagonal' replaces the sum over k < n by the carried term carry_n
     (module docstring).
     """
     rho = np.asarray(rho, dtype=np.float64)
     L = rho.shape[0]
-    comp = solve_components(rho, N, dx0, G, method)
+    triple = method in ("dipole3", "dipole3_ds")
+    comp = solve_components(rho, N, dx0, G, "dipole" if triple else method)
+    if triple:
+        dbl3, two = triple_terms(comp["rho"], Geometry(L, N, dx0), G, quadrupled=method == "dipole3")
     if interp not in ("trilinear", "diagonal"):
         raise ValueError("interp must be 'trilinear' or 'diagonal'")
     out = np.zeros((L, N, N, N))
@@ -216,6 +293,8 @@ def solve(rho, N, dx0, G=1.0, method="original", interp="diagonal"):
     for n in range(L):
         if method == "original" or n == L - 1:
             phi = comp["full"][n].copy()
+        elif triple and n < L - 2:
+            phi = comp["hole"][n] + dbl3[n] + two[n]
         else:
             phi = comp["hole"][n] + comp["dbl"][n]
         if interp == "trilinear":

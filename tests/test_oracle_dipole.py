@@ -1,8 +1,9 @@
 """Pins for the pairwise-dipole ("modified") method of Sect. 7 and Appendix B
-(Eqs. 15, B.1-B.2)."""
+(Eqs. 15, B.1-B.2) and for its three-level extension (Eqs. B.3-B.6)."""
 import numpy as np
+import pytest
 
-from oracle import solve
+from oracle import nested, solve
 from oracle.nested import doubled_fine_potential, Geometry
 from oracle.convolution import direct_sum
 from paper_2301_06763_gb300 import workloads as wl
@@ -87,3 +88,48 @@ def test_modified_close_to_original_for_smooth_density():
     err_a = np.abs(a[0] - an) / np.abs(an)
     err_b = np.abs(b[0] - an) / np.abs(an)
     assert err_b.max() < err_a.max() and err_b.mean() <= err_a.mean()
+
+
+@pytest.mark.parametrize("method", ["dipole3", "dipole3_ds"])
+def test_triple_fft_route_equals_direct_route(method):
+    # Eqs. B.3-B.6: every term of the three-level dipole scheme by the FFT
+    # convolutions (doubled and quadrupled grids) against direct sums at the
+    # sub-cells (2^3 and 4^3 means) or, for Eq. B.6, at the coarse centres
+    from oracle import nested_potential_at
+    N, L, dx0 = 8, 4, 1.0 / 8
+    rho = wl.random_density(31, L, N)
+    out = solve(rho, N, dx0, method=method, interp="trilinear")
+    rng = np.random.default_rng(2)
+    samples = [(n, *map(int, rng.integers(0, N, 3))) for n in range(L) for _ in range(3)]
+    samples += [(0, 0, 0, 0), (1, N - 1, 3, 4), (0, 3, 4, 4)]
+    ref = nested_potential_at(rho, N, dx0, samples, method=method, interp="trilinear")
+    got = np.array([out[s] for s in samples])
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(out))
+
+
+def test_triple_scheme_keeps_a_dipole_two_levels_down():
+    # Sect. 7 / Appendix B: a +-q pair inside one level-1 cell on the finest of
+    # three levels.  The pairwise scheme sees the pair on level 0 only through
+    # level 1's restricted (zero) mass, so level 0 gets nothing; the three-level
+    # scheme reads the finest level on its quadrupled grid and level 0 gets the
+    # dipole field of the pair.
+    N, L, dx0 = 16, 3, 1.0
+    rho = np.zeros((L, N, N, N))
+    rho[2, 8, 8, 8], rho[2, 8, 8, 9] = 1.0, -1.0         # one level-1 cell: x = 8, 9 -> 4
+    two = solve(rho, N, dx0, method="dipole")
+    three = solve(rho, N, dx0, method="dipole3")
+    ds = solve(rho, N, dx0, method="dipole3_ds")
+    assert np.max(np.abs(two[0])) == 0.0
+    # the point-dipole potential of the pair at the level-0 centres, away from it
+    g = nested.Geometry(L, N, dx0)
+    c0, c2 = g.centres(0), g.centres(2)
+    Z, Y, X = np.meshgrid(c0, c0, c0, indexing="ij")
+    m = g.dx(2) ** 3
+    r1 = np.sqrt((X - c2[8]) ** 2 + (Y - c2[8]) ** 2 + (Z - c2[8]) ** 2)
+    r2 = np.sqrt((X - c2[9]) ** 2 + (Y - c2[8]) ** 2 + (Z - c2[8]) ** 2)
+    ref = -m / r1 + m / r2
+    far = r1 > 3 * g.dx(0)
+    for got in (three[0], ds[0]):
+        assert np.corrcoef(got[far], ref[far])[0, 1] > 0.999
+    # Eq. B.6 is the exact point-to-point sum: equal to the reference everywhere
+    assert np.allclose(ds[0], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
