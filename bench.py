@@ -307,82 +307,41 @@ def timed_loop(torch, plan, rhos, phis, steps, dist, stream):
 
 
 def dipole_rates(nm, wl, torch, dev, reps=20):
-    """Pairwise dipole method (Sect. 7, Eqs. B.1-B.2) on 4 levels of 64^3 (two
-    Plummer spheres), against the original method on the same mesh."""
-    w = wl.config_binary()
-    rho = w.rho()
-    out = {"workload": "binary-4x64"}
-    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
-        r = torch.from_numpy(rho).to(dev, dt)
-        phi = torch.empty(rho.shape, dtype=torch.float64, device=dev)
-        for meth in ("original", "dipole"):
-            p = nm.Plan(w.levels, w.N, w.dx0, precision=prec, method=meth)
-            n = reps if prec == "fp32" else max(2, reps // 5)
-            for _ in range(3):
-                p.potential(r, phi)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(n):
-                p.potential(r, phi)
-            b.record()
-            torch.cuda.synchronize()
-            out["%s_%s_ms" % (meth, prec)] = a.elapsed_time(b) / n
-            p.close()
-        out["overhead_%s" % prec] = out["dipole_%s_ms" % prec] / out["original_%s_ms" % prec]
-    return out
-
-
-def accel_rates(nm, torch, dev, rho, w, peak, reps=20, interp=True):
-    """g = -grad Phi (nm_acceleration) on the benchmarked mesh, and the solve
-    with the carried Eqs. 3-6 interpolation against the trilinear one.  The
-    acceleration kernel moves 32 bytes per cell (one double read, three
-    written), over 4 rotating phi/g sets larger than L2."""
-    L, N = w.levels, w.N
-    cells = L * N ** 3
-    p = nm.Plan(L, N, w.dx0, precision="fp64")
-    r = torch.from_numpy(rho).to(dev, torch.float64)
-    phis = [p.potential(r).clone() for _ in range(NSETS)]
-    gs = [torch.empty((L, 3, N, N, N), dtype=torch.float64, device=dev) for _ in range(NSETS)]
-    for i in range(3):
-        p.acceleration(phis[i % NSETS], gs[i % NSETS])
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for i in range(reps):
-        p.acceleration(phis[i % NSETS], gs[i % NSETS])
-    b.record()
-    torch.cuda.synchronize()
-    us = a.elapsed_time(b) / reps * 1e3
-    p.close()
-    del gs
-    gbs = 32.0 * cells / (us * 1e-6) / 1e9
-    # FP64-pipe bound: 3 subtractions and 3 multiplications per interior cell
-    fp64_ops = 6 * cells
-    out = {"acceleration": {"workload": "contrast-%dx%d" % (L, N), "us_per_launch": us,
-                            "algorithmic_bytes": 32 * cells, "gbs": gbs, "frac_hbm": gbs / peak,
-                            "fp64_ops": fp64_ops, "fp64_tops": fp64_ops / (us * 1e-6) / 1e12,
-                            "frac_fp64": fp64_ops / (us * 1e-6) / FP64_OPS_PEAK,
-                            "fp64_peak_ops": FP64_OPS_PEAK}}
-    if not interp:
-        return out
-    diag = {}
-    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
-        rr = torch.from_numpy(rho).to(dev, dt)
-        for interp in ("trilinear", "diagonal"):
-            q = nm.Plan(L, N, w.dx0, precision=prec, interp=interp)
-            n = reps if prec == "fp32" else max(2, reps // 5)
-            for i in range(3):
-                q.potential(rr, phis[i % NSETS])
-            torch.cuda.synchronize()
-            a.record()
-            for i in range(n):
-                q.potential(rr, phis[i % NSETS])
-            b.record()
-            torch.cuda.synchronize()
-            diag["%s_%s_ms" % (interp, prec)] = a.elapsed_time(b) / n
-            q.close()
-    out["interp_readings"] = diag
+    """The dipole schemes (Sect. 7, Appendix B) on 4 levels of 64^3 (two
+    Plummer spheres) and of 32^3, against the original method on the same
+    mesh: pairwise (Eqs. B.1-B.2), three-level with quadrupled grids (Eqs.
+    B.3-B.5) and with the direct sum of Eq. B.6 (FP64 only at 32^3: its O(N^6)
+    sum runs on the slow FP64 pipe)."""
+    out = {}
+    for N in (64, 32):
+        w = wl.config_binary()
+        w = wl.Workload(w.name, w.levels, N, w.dx0 * 64 / N, w.components)
+        rho = w.rho()
+        tag = "binary-4x%d" % N
+        out[tag] = {}
+        for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+            r = torch.from_numpy(rho).to(dev, dt)
+            phi = torch.empty(rho.shape, dtype=torch.float64, device=dev)
+            for meth in ("original", "dipole", "dipole3", "dipole3_ds"):
+                if meth == "dipole3_ds" and prec == "fp64" and N > 32:
+                    continue
+                p = nm.Plan(w.levels, w.N, w.dx0, precision=prec, method=meth)
+                n = reps if prec == "fp32" else max(2, reps // 5)
+                for _ in range(3):
+                    p.potential(r, phi)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(n):
+                    p.potential(r, phi)
+                b.record()
+                torch.cuda.synchronize()
+                out[tag]["%s_%s_ms" % (meth, prec)] = a.elapsed_time(b) / n
+                p.close()
+            for meth in ("dipole", "dipole3", "dipole3_ds"):
+                k = "%s_%s_ms" % (meth, prec)
+                if k in out[tag]:
+                    out[tag]["overhead_%s_%s" % (meth, prec)] = out[tag][k] / out[tag]["original_%s_ms" % prec]
     return out
 
 

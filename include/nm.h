@@ -79,7 +79,7 @@ typedef enum {
 } nm_status;
 
 enum { NM_FP64 = 0, NM_FP32 = 1 };
-enum { NM_METHOD_ORIGINAL = 0, NM_METHOD_DIPOLE_PAIR = 1 };
+enum { NM_METHOD_ORIGINAL = 0, NM_METHOD_DIPOLE_PAIR = 1, NM_METHOD_DIPOLE_TRIPLE = 2, NM_METHOD_DIPOLE_TRIPLE_DIRECT = 3 };
 enum { NM_INTERP_TRILINEAR = 0, NM_INTERP_DIAGONAL = 1 };
 enum { NM_MAX_LEVELS = 16 };
 
@@ -93,8 +93,14 @@ typedef struct {
                         coarser levels' terms in float; Green spectrum built in
                         double; the final per-cell addition of that sum to the
                         level's own potential in double.                        */
-    int method;      /* NM_METHOD_ORIGINAL (Eq. 14) or NM_METHOD_DIPOLE_PAIR
-                        (Eqs. 15, B.1-B.2)                                       */
+    int method;      /* NM_METHOD_ORIGINAL (Eq. 14), NM_METHOD_DIPOLE_PAIR
+                        (Eqs. 15, B.1-B.2), NM_METHOD_DIPOLE_TRIPLE (Eqs. B.3-B.5:
+                        below level L-2 the next level's ring on its doubled
+                        grid and the level after on its quadrupled grid, 4N
+                        cells, transforms of 8N points, so N <= 128) or
+                        NM_METHOD_DIPOLE_TRIPLE_DIRECT (the same with the
+                        quadrupled grid replaced by the direct sum of
+                        Eq. B.6, O(N^6) per level)                              */
     int interp;      /* How the hole potentials reach the finer levels (the
                         stencil of Fig. 6):
                         NM_INTERP_TRILINEAR: tensor-product linear from each

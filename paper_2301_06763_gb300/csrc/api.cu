@@ -263,10 +263,12 @@ struct nm_plan_s {
     int dev = 0;
     int N = 0, L = 0, P = 0;
     bool fp32 = false, dipole = false;
+    bool triple = false, triple_ds = false;   // three-level dipole scheme (Appendix B), Eq. B.6 variant
     size_t es = 8, cs = 16;           // bytes per real / complex value
     nm_schedule sched{1, 16, 0, 1, 1};   // level convolutions
     int group_dbl = 1;                // doubled-grid convolutions in flight
     int npairs = 0, npairs_dbl = 0;
+    int group_qdp = 1, npairs_qdp = 0;   // quadrupled-grid convolutions (three-level scheme)
     int work_slots = 0;               // work buffers allocated (>= sched.group)
     void* restr = nullptr;            // (L-1) * (N/2)^3 restricted densities
     void* work = nullptr;             // work_slots * (P/2) * P^2 complex
@@ -276,13 +278,18 @@ struct nm_plan_s {
     void* vbuf = nullptr;             // method C face arrays, 2 (L-1) 6 (N/2+2)^2 doubles
     void* dbl_work = nullptr;         // group_dbl * (2N) * (4N)^2 complex (dipole)
     void* dbl_out = nullptr;          // (L-1) * (2N)^3 (dipole)
+    void* qdp_work = nullptr;         // group_qdp * (4N) * (8N)^2 complex (three-level scheme)
+    void* qdp_out = nullptr;          // (L-2) * (4N)^3 (three-level scheme, quadrupled grids)
+    void* red = nullptr;              // (L-2) * N^3 reduced quadrupled grids or Eq. B.6 sums
     void* h_rho = nullptr;            // staging for nm_potential_host
     double* h_phi = nullptr;
     size_t ws_bytes = 0;
     Spectrum* spec = nullptr;
     Spectrum* spec_dbl = nullptr;
+    Spectrum* spec_qdp = nullptr;
     Twiddle* tw = nullptr;
     Twiddle* tw_dbl = nullptr;
+    Twiddle* tw_qdp = nullptr;
 };
 
 namespace {
@@ -306,9 +313,13 @@ void plan_free_buffers(nm_plan_t p) {
     cudaFree(p->vbuf);
     cudaFree(p->dbl_work);
     cudaFree(p->dbl_out);
+    cudaFree(p->qdp_work);
+    cudaFree(p->qdp_out);
+    cudaFree(p->red);
     cudaFree(p->h_rho);
     cudaFree(p->h_phi);
     p->restr = p->work = p->lvl = p->crop = p->carry = p->vbuf = p->dbl_work = p->dbl_out = p->h_rho = nullptr;
+    p->qdp_work = p->qdp_out = p->red = nullptr;
     p->h_phi = nullptr;
 }
 
@@ -361,7 +372,7 @@ std::string tune_key(nm_plan_t p) {
         if (c == '"' || c == '|') c = '_';
     char buf[256];
     snprintf(buf, sizeof buf, "%s|N%d|L%d|%s|%s", name.c_str(), p->N, p->L, p->fp32 ? "fp32" : "fp64",
-             p->dipole ? "dipole" : "original");
+             p->triple ? (p->triple_ds ? "dipole3_ds" : "dipole3") : p->dipole ? "dipole" : "original");
     return buf;
 }
 
@@ -480,8 +491,12 @@ static nm_status validate_options(const nm_options& o) {
     if (!(o.dx0 > 0.0) || !std::isfinite(o.dx0)) return fail(NM_EINVAL, "dx0 must be finite and > 0");
     if (!std::isfinite(o.G)) return fail(NM_EINVAL, "G must be finite");
     if (o.precision != NM_FP64 && o.precision != NM_FP32) return fail(NM_EINVAL, "bad precision %d", o.precision);
-    if (o.method != NM_METHOD_ORIGINAL && o.method != NM_METHOD_DIPOLE_PAIR)
+    if (o.method != NM_METHOD_ORIGINAL && o.method != NM_METHOD_DIPOLE_PAIR && o.method != NM_METHOD_DIPOLE_TRIPLE &&
+        o.method != NM_METHOD_DIPOLE_TRIPLE_DIRECT)
         return fail(NM_EINVAL, "bad method %d", o.method);
+    if (o.method == NM_METHOD_DIPOLE_TRIPLE && o.N > 128)
+        return fail(NM_EUNSUPPORTED, "the quadrupled grid of N = %d needs transforms of %d points (at most 1024)", o.N,
+                    8 * o.N);
     if (o.interp != NM_INTERP_TRILINEAR && o.interp != NM_INTERP_DIAGONAL)
         return fail(NM_EINVAL, "bad interp %d", o.interp);
     return NM_OK;
@@ -491,7 +506,7 @@ static nm_status validate_options(const nm_options& o) {
 static size_t default_footprint(const nm_options& o) {
     const size_t N = o.N, L = o.levels, P = 2 * N;
     const size_t es = o.precision == NM_FP32 ? 4 : 8, cs = 2 * es;
-    const bool dipole = o.method == NM_METHOD_DIPOLE_PAIR;
+    const bool dipole = o.method != NM_METHOD_ORIGINAL;
     const size_t N3 = N * N * N, h3 = N3 / 8, nc = N / 2 + 2;
     const int npairs = dipole ? (int)((L + 1) / 2) : (int)L;
     const size_t buf = (P / 2) * P * P * cs;
@@ -502,6 +517,13 @@ static size_t default_footprint(const nm_options& o) {
     if (dipole && L > 1) {
         const size_t buf_dbl = (2 * N) * (4 * N) * (4 * N) * cs;
         b += (size_t)default_group(buf_dbl, (int)(L / 2)) * buf_dbl + (L - 1) * 8 * N3 * es;
+    }
+    if ((o.method == NM_METHOD_DIPOLE_TRIPLE || o.method == NM_METHOD_DIPOLE_TRIPLE_DIRECT) && L > 2) {
+        b += (L - 2) * N3 * es;
+        if (o.method == NM_METHOD_DIPOLE_TRIPLE) {
+            const size_t buf_qdp = (4 * N) * (8 * N) * (8 * N) * cs;
+            b += (size_t)default_group(buf_qdp, (int)((L - 1) / 2)) * buf_qdp + (L - 2) * 64 * N3 * es;
+        }
     }
     return b;
 }
@@ -533,7 +555,9 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     p->L = o.levels;
     p->P = 2 * o.N;
     p->fp32 = o.precision == NM_FP32;
-    p->dipole = o.method == NM_METHOD_DIPOLE_PAIR;
+    p->dipole = o.method != NM_METHOD_ORIGINAL;
+    p->triple = (o.method == NM_METHOD_DIPOLE_TRIPLE || o.method == NM_METHOD_DIPOLE_TRIPLE_DIRECT) && o.levels > 2;
+    p->triple_ds = o.method == NM_METHOD_DIPOLE_TRIPLE_DIRECT;
     p->es = p->fp32 ? 4 : 8;
     p->cs = 2 * p->es;
     const size_t N = o.N, L = o.levels;
@@ -550,6 +574,9 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     if (tune_lookup(p, &tuned) && sched_valid(p, tuned)) p->sched = tuned;
     const size_t buf_dbl = (2 * N) * (4 * N) * (4 * N) * p->cs;
     if (p->dipole) p->group_dbl = default_group(buf_dbl, p->npairs_dbl);
+    const size_t buf_qdp = (4 * N) * (8 * N) * (8 * N) * p->cs;
+    p->npairs_qdp = p->triple && !p->triple_ds ? (int)((L - 1) / 2) : 0;   // ceil((L-2)/2)
+    if (p->npairs_qdp) p->group_qdp = default_group(buf_qdp, p->npairs_qdp);
 
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** ptr, size_t bytes) {
@@ -568,6 +595,11 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
         alloc(&p->dbl_work, (size_t)p->group_dbl * buf_dbl);
         alloc(&p->dbl_out, (L - 1) * 8 * N3 * p->es);
     }
+    if (p->triple) alloc(&p->red, (L - 2) * N3 * p->es);
+    if (p->npairs_qdp) {
+        alloc(&p->qdp_work, (size_t)p->group_qdp * buf_qdp);
+        alloc(&p->qdp_out, (L - 2) * 64 * N3 * p->es);
+    }
     if (e != cudaSuccess) {
         plan_free_buffers(p);
         delete p;
@@ -575,11 +607,14 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     }
     nm_status st = get_twiddle(p->dev, p->P, &p->tw);
     if (st == NM_OK && p->dipole && L > 1) st = get_twiddle(p->dev, 2 * p->P, &p->tw_dbl);
+    if (st == NM_OK && p->npairs_qdp) st = get_twiddle(p->dev, 4 * p->P, &p->tw_qdp);
     if (st == NM_OK) st = acquire_spectrum(p->dev, o.N, &p->spec);
     if (st == NM_OK && p->dipole && L > 1) st = acquire_spectrum(p->dev, 2 * o.N, &p->spec_dbl);
+    if (st == NM_OK && p->npairs_qdp) st = acquire_spectrum(p->dev, 4 * o.N, &p->spec_qdp);
     if (st != NM_OK) {
         release_spectrum(p->spec);
         release_spectrum(p->spec_dbl);
+        release_spectrum(p->spec_qdp);
         plan_free_buffers(p);
         delete p;
         return st;
@@ -598,6 +633,7 @@ nm_status nm_green(nm_plan_t p, void* stream) {
     if (!p) return fail(NM_EINVAL, "nm_green: null plan");
     nm_status st = build_spectrum(p->spec, (cudaStream_t)stream);
     if (st == NM_OK && p->spec_dbl) st = build_spectrum(p->spec_dbl, (cudaStream_t)stream);
+    if (st == NM_OK && p->spec_qdp) st = build_spectrum(p->spec_qdp, (cudaStream_t)stream);
     return st;
 }
 
@@ -675,8 +711,32 @@ void dbl_pairs(nm_plan_t p, const void* rho, std::vector<PairDesc<T>>& out) {
         for (int h = 0; h < 2; ++h) {
             const int nn = n + h;
             if (nn < L - 1) {
-                d.src[h] = field(p, rho, nn + 1, SRC_FULL, P2);
+                // three-level scheme: level n+1's ring only (level n+2's
+                // region emptied) below level L-2, Fig. App0
+                const int mode = (p->triple && nn < L - 2) ? SRC_HOLE : SRC_FULL;
+                d.src[h] = field(p, rho, nn + 1, mode, P2);
                 d.dst[h] = {(T*)p->dbl_out + (size_t)nn * 8 * N3, DST_GRID};
+            } else {
+                d.src[h] = kNoSrc;
+                d.dst[h] = {nullptr, DST_NONE};
+            }
+        }
+        out.push_back(d);
+    }
+}
+
+// Quadrupled grids (Fig. App0): level n+2's mass on 4N cells spanning level n.
+template <typename T>
+void qdp_pairs(nm_plan_t p, const void* rho, std::vector<PairDesc<T>>& out) {
+    const int L = p->L, P4 = 4 * p->P;
+    const size_t N3 = (size_t)p->N * p->N * p->N;
+    for (int n = 0; n < L - 2; n += 2) {
+        PairDesc<T> d{};
+        for (int h = 0; h < 2; ++h) {
+            const int nn = n + h;
+            if (nn < L - 2) {
+                d.src[h] = field(p, rho, nn + 2, SRC_FULL, P4);
+                d.dst[h] = {(T*)p->qdp_out + (size_t)nn * 64 * N3, DST_GRID};
             } else {
                 d.src[h] = kNoSrc;
                 d.dst[h] = {nullptr, DST_NONE};
@@ -694,8 +754,13 @@ template <> const cpx<float>* tw_of<float>(const Twiddle* t) { return t->d32; }
 template <> const cpx<double>* tw_of<double>(const Twiddle* t) { return t->d64; }
 
 template <typename T>
-cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, bool dbl, const nm_schedule& sc,
+cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, int geom, const nm_schedule& sc,
                      const T* spec, const cpx<T>* tw, cudaStream_t s) {
+    if (geom == 2) {
+        if constexpr (sizeof(T) == 4) return run_conv_qdp_f32(pairs, n, P, spec, tw, s);
+        else return run_conv_qdp_f64(pairs, n, P, spec, tw, s);
+    }
+    const bool dbl = geom == 1;
     const bool e16 = dbl || (sc.radix == 16 && P >= 16);
     const int flags = (sc.tile ? CONV_WIDE : 0) | (sc.pipeline ? CONV_TMA : 0) | (sc.fuse ? CONV_FUSED : 0);
     if constexpr (sizeof(T) == 4) {
@@ -709,14 +774,8 @@ cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, bool dbl, const nm_
 
 template <typename T>
 nm_status enqueue_restrict(nm_plan_t p, const void* rho, cudaStream_t s) {
-    const int L = p->L, N = p->N;
-    const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
-    for (int m = L - 2; m >= 0; --m) {
-        const T* child = (const T*)rho + (size_t)(m + 1) * N3;
-        const T* rchild = (m + 1 < L - 1) ? (const T*)p->restr + (size_t)(m + 1) * h3 : nullptr;
-        cudaError_t e = run_restrict<T>(child, rchild, (T*)p->restr + (size_t)m * h3, N, s);
-        if (e != cudaSuccess) return cuda_fail(e, "restriction");
-    }
+    cudaError_t e = run_restrict_chain<T>((const T*)rho, (T*)p->restr, p->L, p->N, s);
+    if (e != cudaSuccess) return cuda_fail(e, "restriction");
     return NM_OK;
 }
 
@@ -733,6 +792,7 @@ nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
     for (int n = 0; n < L; ++n) {
         a.base[n] = lvl + (size_t)n * N3;
         a.dbl[n] = (p->dipole && n < L - 1) ? (const T*)p->dbl_out + (size_t)n * 8 * N3 : nullptr;
+        a.red[n] = (p->triple && n < L - 2) ? (const T*)p->red + (size_t)n * N3 : nullptr;
         if (n < L - 1) {
             if (p->dipole) {
                 a.interp[n] = lvl + (size_t)n * N3;
@@ -766,18 +826,18 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
     nm_status st;
     for (const Item& it : items)
         if ((st = enqueue_restrict<T>(it.p, it.rho, s)) != NM_OK) return st;
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool dbl = pass == 1;
+    // geometry 0: level grids; 1: doubled grids (dipole methods); 2:
+    // quadrupled grids (three-level scheme)
+    for (int geom = 0; geom < 3; ++geom) {
         std::vector<std::vector<PairDesc<T>>> pl(items.size());
         int rounds = 0;
+        auto group_of = [&](nm_plan_t p) { return geom == 0 ? p->sched.group : geom == 1 ? p->group_dbl : p->group_qdp; };
         for (size_t i = 0; i < items.size(); ++i) {
             nm_plan_t p = items[i].p;
-            if (dbl) {
-                if (p->dipole && p->L > 1) dbl_pairs<T>(p, items[i].rho, pl[i]);
-            } else {
-                level_pairs<T>(p, items[i].rho, pl[i]);
-            }
-            const int g = dbl ? p->group_dbl : p->sched.group;
+            if (geom == 0) level_pairs<T>(p, items[i].rho, pl[i]);
+            else if (geom == 1 && p->dipole && p->L > 1) dbl_pairs<T>(p, items[i].rho, pl[i]);
+            else if (geom == 2 && p->npairs_qdp) qdp_pairs<T>(p, items[i].rho, pl[i]);
+            const int g = group_of(p);
             const int r = ((int)pl[i].size() + g - 1) / g;
             if (r > rounds) rounds = r;
         }
@@ -792,11 +852,13 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
             std::vector<Bucket> buckets;
             for (size_t i = 0; i < items.size(); ++i) {
                 nm_plan_t p = items[i].p;
-                const int g = dbl ? p->group_dbl : p->sched.group;
-                const int P = dbl ? 2 * p->P : p->P;
-                const nm_schedule sc = dbl ? nm_schedule{1, 16, 0, 0, 0} : p->sched;
+                const int g = group_of(p);
+                const int P = p->P << geom;
+                const nm_schedule sc = geom ? nm_schedule{1, 16, 0, 0, 0} : p->sched;
                 const size_t buf = (size_t)(P / 2) * P * P;
-                cpx<T>* work = (cpx<T>*)(dbl ? p->dbl_work : p->work);
+                cpx<T>* work = (cpx<T>*)(geom == 0 ? p->work : geom == 1 ? p->dbl_work : p->qdp_work);
+                const Spectrum* spec = geom == 0 ? p->spec : geom == 1 ? p->spec_dbl : p->spec_qdp;
+                const Twiddle* tw = geom == 0 ? p->tw : geom == 1 ? p->tw_dbl : p->tw_qdp;
                 for (int q = r * g; q < (r + 1) * g && q < (int)pl[i].size(); ++q) {
                     PairDesc<T> d = pl[i][q];
                     d.work = work + (size_t)(q - r * g) * buf;
@@ -806,18 +868,41 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
                             bb.sc.pipeline == sc.pipeline && bb.sc.fuse == sc.fuse)
                             b = &bb;
                     if (!b) {
-                        buckets.push_back({P, sc, spec_of<T>(dbl ? p->spec_dbl : p->spec),
-                                           tw_of<T>(dbl ? p->tw_dbl : p->tw), {}});
+                        buckets.push_back({P, sc, spec_of<T>(spec), tw_of<T>(tw), {}});
                         b = &buckets.back();
                     }
                     b->pairs.push_back(d);
                 }
             }
             for (auto& b : buckets) {
-                cudaError_t e = run_conv<T>(b.pairs.data(), (int)b.pairs.size(), b.P, dbl, b.sc, b.spec,
+                cudaError_t e = run_conv<T>(b.pairs.data(), (int)b.pairs.size(), b.P, geom, b.sc, b.spec,
                                             b.tw, s);
-                if (e != cudaSuccess) return cuda_fail(e, dbl ? "doubled-grid convolution" : "level convolution");
+                if (e != cudaSuccess)
+                    return cuda_fail(e, geom == 0   ? "level convolution"
+                                        : geom == 1 ? "doubled-grid convolution"
+                                                    : "quadrupled-grid convolution");
             }
+        }
+    }
+    // three-level scheme: level n+2's term on level n (n < L-2), reduced from
+    // the quadrupled grid or summed directly (Eq. B.6)
+    for (const Item& it : items) {
+        nm_plan_t p = it.p;
+        if (!p->triple) continue;
+        const int N = p->N;
+        const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
+        for (int n = 0; n + 2 < p->L; ++n) {
+            T* out = (T*)p->red + (size_t)n * N3;
+            cudaError_t e;
+            if (p->triple_ds) {
+                const int m = n + 2;
+                const double dx = p->opt.dx0 / std::ldexp(1.0, m);
+                const T* restr = m < p->L - 1 ? (const T*)p->restr + (size_t)m * h3 : nullptr;
+                e = run_direct2<T>((const T*)it.rho + (size_t)m * N3, restr, out, N, -p->opt.G * dx * dx, s);
+            } else {
+                e = run_reduce4<T>((const T*)p->qdp_out + (size_t)n * 64 * N3, out, N, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "three-level term");
         }
     }
     for (const Item& it : items)
@@ -826,7 +911,8 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
 }
 
 nm_status ensure_green(nm_plan_t p, cudaStream_t s) {
-    if (!p->spec->ready || (p->spec_dbl && !p->spec_dbl->ready)) return nm_green(p, (void*)s);
+    if (!p->spec->ready || (p->spec_dbl && !p->spec_dbl->ready) || (p->spec_qdp && !p->spec_qdp->ready))
+        return nm_green(p, (void*)s);
     return NM_OK;
 }
 
@@ -1083,6 +1169,7 @@ nm_status nm_spectrum_bytes(nm_plan_t p, size_t* bytes) {
     if (!p || !bytes) return fail(NM_EINVAL, "nm_spectrum_bytes: null argument");
     size_t b = octant_count(p->N) * (sizeof(double) + sizeof(float));
     if (p->spec_dbl) b += octant_count(2 * p->N) * (sizeof(double) + sizeof(float));
+    if (p->spec_qdp) b += octant_count(4 * p->N) * (sizeof(double) + sizeof(float));
     *bytes = b;
     return NM_OK;
 }
@@ -1111,6 +1198,7 @@ nm_status nm_destroy(nm_plan_t p) {
     plan_free_buffers(p);
     release_spectrum(p->spec);
     release_spectrum(p->spec_dbl);
+    release_spectrum(p->spec_qdp);
     delete p;
     if (e != cudaSuccess) return cuda_fail(e, "nm_destroy sync");
     return NM_OK;

@@ -6,13 +6,16 @@
 // convolution of the packed field is conv(re) + i*conv(im) and both come back
 // from one complex transform.
 //
-// Domain: FFT size P per axis.  Two geometries share the code:
-//   level grid (DBL = false): an N^3 block, N = P/2, sits at [0, N) (Fig. 4:
-//       the active region 1, regions 2-4 zero);
-//   doubled fine grid (DBL = true, Sect. 7 / Fig. 16): the fine level's N^3
-//       block sits at [N/2, 3N/2) of a 2N-cell grid, N = P/4, period P = 4N;
-//       any period >= 3N - 1 keeps the sum isolated.
-// In both the output window is [0, P/2) per axis.
+// Domain: FFT size P per axis.  Three geometries (GM) share the code:
+//   0 level grid: an N^3 block, N = P/2, sits at [0, N) (Fig. 4: the active
+//       region 1, regions 2-4 zero);
+//   1 doubled fine grid (Sect. 7 / Fig. 16): the fine level's N^3 block sits
+//       at [N/2, 3N/2) of a 2N-cell grid, N = P/4, period P = 4N; any period
+//       >= 3N - 1 keeps the sum isolated;
+//   2 quadrupled grid (Appendix B / Fig. App0): a level's N^3 block sits at
+//       [3N/2, 5N/2) of a 4N-cell grid spanning the level two steps coarser,
+//       N = P/8, period P = 8N (>= 5N - 1).
+// In all three the output window is [0, P/2) per axis.
 //
 // Work buffer of one pair: [Z = P/2][P][P] complex, index (z*P + y)*P + x.
 //   1 xfwd : rows (z, y) of the input block: mask, scale, pack, pad, FFT along x
@@ -100,20 +103,21 @@ __device__ __forceinline__ cpx<T> src_pair(const SrcField& f0, const SrcField& f
     return {src_value<T, TIN>(f0, s0, NL, z, y, x), src_value<T, TIN>(f1, s1, NL, z, y, x)};
 }
 
-template <int P, int E, bool DBL> struct Geo {
-    static constexpr int NIN = DBL ? P / 4 : P / 2;   // input block extent
-    static constexpr int OFF = DBL ? P / 8 : 0;       // its offset in the domain
-    static constexpr int NOUT = P / 2;                // output window
+template <int P, int E, int GM> struct Geo {
+    static_assert(GM != 2 || E == 16, "the quadrupled grid needs 16 values per thread");
+    static constexpr int NIN = GM == 0 ? P / 2 : GM == 1 ? P / 4 : P / 8;         // input block extent
+    static constexpr int OFF = GM == 0 ? 0 : GM == 1 ? P / 8 : 3 * P / 16;        // its offset in the domain
+    static constexpr int NOUT = P / 2;                                            // output window
     // first-pass register r holds x[j + r P/E]: nonzero only for these r
     __device__ static constexpr bool live(int r) {
-        return DBL ? (r >= E / 8 && r < 3 * E / 8) : (r < E / 2);
+        return GM == 0 ? (r < E / 2) : GM == 1 ? (r >= E / 8 && r < 3 * E / 8) : (r >= 3 * E / 16 && r < 5 * E / 16);
     }
 };
 
 // ---------------------------------------------------------------- pass 1
-template <typename T, typename TIN, int P, int E, bool DBL>
+template <typename T, typename TIN, int P, int E, int GM>
 __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T> a) {
-    using G = Geo<P, E, DBL>;
+    using G = Geo<P, E, GM>;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
     // contiguous in it, so stage them through shared memory with 16-byte
     // loads (more bytes in flight per instruction than the transform's
     // strided layout allows) and read the transform layout from there.
-    const bool staged = !DBL && d.src[0].mode == SRC_FULL && d.src[0].rho == d.src[1].rho &&
+    const bool staged = GM == 0 && d.src[0].mode == SRC_FULL && d.src[0].rho == d.src[1].rho &&
                         (d.src[1].mode == SRC_HOLE || d.src[1].mode == SRC_NONE) &&
                         (((uintptr_t)d.src[0].rho & 15) == 0);
     if (staged) {
@@ -185,15 +189,18 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
 }
 
 // ---------------------------------------------------------------- passes 2, 4
-template <typename T, int P, int E, int TX, bool INV, bool DBL>
+template <typename T, int P, int E, int TX, bool INV, int GM>
 __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ ConvArgs<T> a) {
-    using G = Geo<P, E, DBL>;
+    using G = Geo<P, E, GM>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
     const PairDesc<T>& d = a.pair[blockIdx.z];
     load_twiddles(sm_tw, a.tw, P);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
+    // blockDim.x = TX P/E: lets the compiler see which outputs of the last
+    // pass the window keeps, and drop the rest
+    __builtin_assume(j < P / E);
     const int z = (INV ? 0 : G::OFF) + blockIdx.y;
     const int x = blockIdx.x * TX + l;
     cpx<T>* slab = d.work + (size_t)z * P * P;
@@ -215,10 +222,10 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
 // ---------------------------------------------------------------- pass 3
 // At least 1024 resident threads per SM (4 CTAs of 256): the seam holds two
 // transforms' worth of live values, and more warps hide its load latency.
-template <typename T, int P, int E, int TX, bool DBL>
+template <typename T, int P, int E, int TX, int GM>
 __global__ void __launch_bounds__(TX * P / E, (1024 / (TX * P / E)) > 0 ? 1024 / (TX * P / E) : 1)
     k_zseam(const __grid_constant__ ConvArgs<T> a) {
-    using G = Geo<P, E, DBL>;
+    using G = Geo<P, E, GM>;
     constexpr int H = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -226,6 +233,9 @@ __global__ void __launch_bounds__(TX * P / E, (1024 / (TX * P / E)) > 0 ? 1024 /
     const PairDesc<T>& d = a.pair[blockIdx.z];
     load_twiddles(sm_tw, a.tw, P);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
+    // blockDim.x = TX P/E: lets the compiler see which outputs of the last
+    // pass the window keeps, and drop the rest
+    __builtin_assume(j < P / E);
     const int y = blockIdx.y;
     const int x = blockIdx.x * TX + l;
     cpx<T>* col = d.work + (size_t)y * P + x;          // element z at col[z * P * P]
@@ -272,7 +282,7 @@ __device__ __forceinline__ void store_out(const DstField& f, int z, int y, int x
     }
 }
 
-template <typename T, int P, int E, bool DBL>
+template <typename T, int P, int E, int GM>
 __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T> a) {
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;

@@ -67,10 +67,10 @@ static cudaError_t fused_pass(const ConvArgs<T>& a, int np, bool fwd, cudaStream
 }
 
 // W = requested column-tile width of the strided passes.
-template <typename T, int P, int E, int W, bool DBL>
+template <typename T, int P, int E, int W, int GM>
 static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStream_t s) {
     const bool tma = (flags & CONV_TMA) != 0;
-    if constexpr (!DBL && E == 16 && FusedShape<T, P>::OK) {
+    if constexpr (GM == 0 && E == 16 && FusedShape<T, P>::OK) {
         if (flags & CONV_FUSED) {
             constexpr int TX = Tile<P, E, W>::TX;
             const char* tag = sizeof(T) == 4 ? "f32" : "f64";
@@ -103,7 +103,7 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
             return cudaGetLastError();
         }
     }
-    using Gm = Geo<P, E, DBL>;
+    using Gm = Geo<P, E, GM>;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     constexpr int TX = Tile<P, E, W>::TX;
@@ -114,51 +114,51 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
     // shared-memory limits are set once per kernel (thread-safe static init)
     static const cudaError_t prepared = [&]() {
         cudaError_t e;
-        if ((e = prep_kernel(k_xfwd<T, T, P, E, DBL>, sm_x)) != cudaSuccess) return e;
-        if ((e = prep_kernel(k_ypass<T, P, E, TX, false, DBL>, sm_yz)) != cudaSuccess) return e;
-        if ((e = prep_kernel(k_zseam<T, P, E, TX, DBL>, sm_yz)) != cudaSuccess) return e;
-        if ((e = prep_kernel(k_ypass<T, P, E, TX, true, DBL>, sm_yz)) != cudaSuccess) return e;
-        return prep_kernel(k_xinv<T, P, E, DBL>, sm_x);
+        if ((e = prep_kernel(k_xfwd<T, T, P, E, GM>, sm_x)) != cudaSuccess) return e;
+        if ((e = prep_kernel(k_ypass<T, P, E, TX, false, GM>, sm_yz)) != cudaSuccess) return e;
+        if ((e = prep_kernel(k_zseam<T, P, E, TX, GM>, sm_yz)) != cudaSuccess) return e;
+        if ((e = prep_kernel(k_ypass<T, P, E, TX, true, GM>, sm_yz)) != cudaSuccess) return e;
+        return prep_kernel(k_xinv<T, P, E, GM>, sm_x);
     }();
     if (prepared != cudaSuccess) return prepared;
     const int rows_in = Gm::NIN * Gm::NIN;
     const int rows_out = Gm::NOUT * Gm::NOUT;
     char nm_[48];
     const char* tag = sizeof(T) == 4 ? "f32" : "f64";
-    const char* geo = DBL ? "_dbl" : "";
+    const char* geo = GM == 1 ? "_dbl" : GM == 2 ? "_qdp" : "";
     {
         snprintf(nm_, sizeof nm_, "xfwd%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_xfwd<T, T, P, E, DBL><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        k_xfwd<T, T, P, E, GM><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "yfwd%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_ypass<T, P, E, TX, false, DBL><<<dim3(P / TX, Gm::NIN, np), NT, sm_yz, s>>>(a);
+        k_ypass<T, P, E, TX, false, GM><<<dim3(P / TX, Gm::NIN, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        if constexpr (!DBL) {
+        if constexpr (GM == 0) {
             if (tma) {
                 cudaError_t e = zseam_tma<T, P, E, TX>(a, np, s);
                 if (e != cudaSuccess) return e;
             } else {
-                k_zseam<T, P, E, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+                k_zseam<T, P, E, TX, GM><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
             }
         } else {
-            k_zseam<T, P, E, TX, DBL><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+            k_zseam<T, P, E, TX, GM><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
         }
     }
     {
         snprintf(nm_, sizeof nm_, "yinv%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_ypass<T, P, E, TX, true, DBL><<<dim3(P / TX, Gm::NOUT, np), NT, sm_yz, s>>>(a);
+        k_ypass<T, P, E, TX, true, GM><<<dim3(P / TX, Gm::NOUT, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "xinv%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_xinv<T, P, E, DBL><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        k_xinv<T, P, E, GM><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     count_launches(5);
     return cudaGetLastError();
@@ -171,10 +171,10 @@ template <typename T> struct Widths {
     static constexpr int WIDE = 2 * NARROW;
 };
 
-template <typename T, int P, int E, bool DBL>
+template <typename T, int P, int E, int GM>
 static cudaError_t conv_width(const ConvArgs<T>& a, int np, int flags, cudaStream_t s) {
-    if (flags & CONV_WIDE) return conv_passes<T, P, E, Widths<T>::WIDE, DBL>(a, np, flags, s);
-    return conv_passes<T, P, E, Widths<T>::NARROW, DBL>(a, np, flags, s);
+    if (flags & CONV_WIDE) return conv_passes<T, P, E, Widths<T>::WIDE, GM>(a, np, flags, s);
+    return conv_passes<T, P, E, Widths<T>::NARROW, GM>(a, np, flags, s);
 }
 
 // The doubled-grid geometry is instantiated only with the default schedule
@@ -185,29 +185,60 @@ static cudaError_t conv_dispatch(const ConvArgs<T>& a, int np, int P, bool dbl, 
     if (dbl) {
         if constexpr (E == 16) {
             switch (P) {
-                case 16: return conv_passes<T, 16, 16, Widths<T>::NARROW, true>(a, np, 0, s);
-                case 32: return conv_passes<T, 32, 16, Widths<T>::NARROW, true>(a, np, 0, s);
-                case 64: return conv_passes<T, 64, 16, Widths<T>::NARROW, true>(a, np, 0, s);
-                case 128: return conv_passes<T, 128, 16, Widths<T>::NARROW, true>(a, np, 0, s);
-                case 256: return conv_passes<T, 256, 16, Widths<T>::NARROW, true>(a, np, 0, s);
-                case 512: return conv_passes<T, 512, 16, Widths<T>::NARROW, true>(a, np, 0, s);
-                case 1024: return conv_passes<T, 1024, 16, Widths<T>::NARROW, true>(a, np, 0, s);
+                case 16: return conv_passes<T, 16, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
+                case 32: return conv_passes<T, 32, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
+                case 64: return conv_passes<T, 64, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
+                case 128: return conv_passes<T, 128, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
+                case 256: return conv_passes<T, 256, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
+                case 512: return conv_passes<T, 512, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
+                case 1024: return conv_passes<T, 1024, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
                 default: break;
             }
         }
         return cudaErrorInvalidValue;
     }
     switch (P) {
-        case 8: if constexpr (E == 8) return conv_width<T, 8, 8, false>(a, np, flags, s); break;
-        case 16: return conv_width<T, 16, E, false>(a, np, flags, s);
-        case 32: return conv_width<T, 32, E, false>(a, np, flags, s);
-        case 64: return conv_width<T, 64, E, false>(a, np, flags, s);
-        case 128: return conv_width<T, 128, E, false>(a, np, flags, s);
-        case 256: return conv_width<T, 256, E, false>(a, np, flags, s);
-        case 512: return conv_width<T, 512, E, false>(a, np, flags, s);
+        case 8: if constexpr (E == 8) return conv_width<T, 8, 8, 0>(a, np, flags, s); break;
+        case 16: return conv_width<T, 16, E, 0>(a, np, flags, s);
+        case 32: return conv_width<T, 32, E, 0>(a, np, flags, s);
+        case 64: return conv_width<T, 64, E, 0>(a, np, flags, s);
+        case 128: return conv_width<T, 128, E, 0>(a, np, flags, s);
+        case 256: return conv_width<T, 256, E, 0>(a, np, flags, s);
+        case 512: return conv_width<T, 512, E, 0>(a, np, flags, s);
         default: break;
     }
     return cudaErrorInvalidValue;
+}
+
+// The quadrupled-grid geometry (E = 16, narrow tiles), P = 8N for N = 4 ..
+// 128; instantiated only by the translation units that call it.
+template <typename T>
+static cudaError_t conv_dispatch_qdp(const ConvArgs<T>& a, int np, int P, cudaStream_t s) {
+    switch (P) {
+        case 32: return conv_passes<T, 32, 16, Widths<T>::NARROW, 2>(a, np, 0, s);
+        case 64: return conv_passes<T, 64, 16, Widths<T>::NARROW, 2>(a, np, 0, s);
+        case 128: return conv_passes<T, 128, 16, Widths<T>::NARROW, 2>(a, np, 0, s);
+        case 256: return conv_passes<T, 256, 16, Widths<T>::NARROW, 2>(a, np, 0, s);
+        case 512: return conv_passes<T, 512, 16, Widths<T>::NARROW, 2>(a, np, 0, s);
+        case 1024: return conv_passes<T, 1024, 16, Widths<T>::NARROW, 2>(a, np, 0, s);
+        default: break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t run_conv_qdp_variant(const PairDesc<T>* pairs, int npairs, int P, const T* spec,
+                                        const cpx<T>* tw, cudaStream_t s) {
+    ConvArgs<T> a;
+    a.spec = spec;
+    a.tw = tw;
+    for (int i0 = 0; i0 < npairs; i0 += kMaxPairs) {
+        const int np = npairs - i0 < kMaxPairs ? npairs - i0 : kMaxPairs;
+        for (int i = 0; i < np; ++i) a.pair[i] = pairs[i0 + i];
+        cudaError_t e = conv_dispatch_qdp<T>(a, np, P, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T, int E>

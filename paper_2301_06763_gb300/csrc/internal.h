@@ -25,8 +25,8 @@ struct ProfScope {
 // one entry point per (precision, values per thread).  `flags`: CONV_WIDE
 // selects the wider column tile, CONV_TMA the persistent TMA-fed z-seam,
 // CONV_FUSED the cluster-fused x/y passes (level grids only; 16 values per
-// thread; sizes whose slab does not fit a cluster keep the five passes).  DBL selects the doubled-fine-grid geometry (16 values,
-// narrow tiles only).  Returns the first launch error.
+// thread; sizes whose slab does not fit a cluster keep the five passes).  `dbl` selects the doubled-fine-grid geometry (16
+// values, narrow tiles only).  Returns the first launch error.
 enum { CONV_WIDE = 1, CONV_TMA = 2, CONV_FUSED = 4 };
 cudaError_t run_conv_f32_e16(const PairDesc<float>* pairs, int npairs, int P, bool dbl, int flags,
                              const float* spec, const cpx<float>* tw, cudaStream_t s);
@@ -36,6 +36,11 @@ cudaError_t run_conv_f64_e16(const PairDesc<double>* pairs, int npairs, int P, b
                              const double* spec, const cpx<double>* tw, cudaStream_t s);
 cudaError_t run_conv_f64_e8(const PairDesc<double>* pairs, int npairs, int P, bool dbl, int flags,
                             const double* spec, const cpx<double>* tw, cudaStream_t s);
+// Quadrupled-grid geometry (Appendix B), P = 8N, 16 values per thread.
+cudaError_t run_conv_qdp_f32(const PairDesc<float>* pairs, int npairs, int P, const float* spec,
+                             const cpx<float>* tw, cudaStream_t s);
+cudaError_t run_conv_qdp_f64(const PairDesc<double>* pairs, int npairs, int P, const double* spec,
+                             const cpx<double>* tw, cudaStream_t s);
 
 // TMA descriptor of one work buffer ([P/2][P][P] complex, seen as
 // [P/2][P][2P] reals) with a box of TX columns x 1 row x P/2 slabs.
@@ -58,10 +63,16 @@ template <typename TIN>
 cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* restr_out, int N,
                          cudaStream_t s);
 
+// The whole restriction sweep (levels L-2 .. 0) in one cooperative launch.
+template <typename TIN>
+cudaError_t run_restrict_chain(const TIN* rho, TIN* restr, int L, int N, cudaStream_t s);
+
 // Final assembly (Eq. 14 / Eqs. 15, B.1-B.2) into phi (double).
 template <typename T> struct AssembleArgs {
     const T* base[16];     // per level: Phi^n (original) or Phi^n_hole (dipole), N^3
     const T* dbl[16];      // per level: (2N)^3 doubled-grid potential to reduce, or null
+    const T* red[16];      // per level: an N^3 term added as it is (the reduced quadrupled
+                           // grid or the direct sum of the three-level scheme), or null
     const T* interp[16];   // per level k: source of the hole potential for finer levels
     int interp_origin[16]; // level-k index of interp[k]'s first cell on each axis
     int interp_extent[16]; // its extent per axis
@@ -88,6 +99,17 @@ template <typename T>
 cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStream_t s);
 template <typename T>
 cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s);
+
+// Three-level dipole scheme (dipole3.cu): out (N^3) = mean of each 4^3 block
+// of in ((4N)^3); and Eq. B.6, out (N^3, level n centres) = scale * sum over
+// the N^3 cells j of level n+2 of rho_j / |u_i - j| in level-(n+2) cell units
+// (u_i = 4 i + 3/2 - 3N/2 per axis), rho_j from `rho` with the covered cells
+// taken from `restr` ((N/2)^3, or null), scale = -G dx_{n+2}^2; float sums are
+// carried in double across source tiles.
+template <typename T>
+cudaError_t run_reduce4(const T* in, T* out, int N, cudaStream_t s);
+template <typename T>
+cudaError_t run_direct2(const T* rho, const T* restr, T* out, int N, double scale, cudaStream_t s);
 
 // g = -grad Phi of a nested potential (accel.cu).
 cudaError_t run_accel(const double* phi, double* g, int levels, int N, double dx0, cudaStream_t s);
