@@ -345,6 +345,61 @@ def dipole_rates(nm, wl, torch, dev, reps=20):
     return out
 
 
+def accel_rates(nm, torch, dev, rho, w, peak, reps=20, interp=True):
+    """g = -grad Phi (nm_acceleration) on the benchmarked mesh, and the solve
+    with the carried Eqs. 3-6 interpolation against the trilinear one.  The
+    acceleration kernel moves 32 bytes per cell (one double read, three
+    written), over 4 rotating phi/g sets larger than L2."""
+    L, N = w.levels, w.N
+    cells = L * N ** 3
+    p = nm.Plan(L, N, w.dx0, precision="fp64")
+    r = torch.from_numpy(rho).to(dev, torch.float64)
+    phis = [p.potential(r).clone() for _ in range(NSETS)]
+    gs = [torch.empty((L, 3, N, N, N), dtype=torch.float64, device=dev) for _ in range(NSETS)]
+    for i in range(3):
+        p.acceleration(phis[i % NSETS], gs[i % NSETS])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for i in range(reps):
+        p.acceleration(phis[i % NSETS], gs[i % NSETS])
+    b.record()
+    torch.cuda.synchronize()
+    us = a.elapsed_time(b) / reps * 1e3
+    p.close()
+    del gs
+    gbs = 32.0 * cells / (us * 1e-6) / 1e9
+    # FP64-pipe bound: 3 subtractions and 3 multiplications per interior cell
+    fp64_ops = 6 * cells
+    out = {"acceleration": {"workload": "contrast-%dx%d" % (L, N), "us_per_launch": us,
+                            "algorithmic_bytes": 32 * cells, "gbs": gbs, "frac_hbm": gbs / peak,
+                            "fp64_ops": fp64_ops, "fp64_tops": fp64_ops / (us * 1e-6) / 1e12,
+                            "frac_fp64": fp64_ops / (us * 1e-6) / FP64_OPS_PEAK,
+                            "fp64_peak_ops": FP64_OPS_PEAK}}
+    if not interp:
+        return out
+    diag = {}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        rr = torch.from_numpy(rho).to(dev, dt)
+        for interp in ("trilinear", "diagonal"):
+            q = nm.Plan(L, N, w.dx0, precision=prec, interp=interp)
+            n = reps if prec == "fp32" else max(2, reps // 5)
+            for i in range(3):
+                q.potential(rr, phis[i % NSETS])
+            torch.cuda.synchronize()
+            a.record()
+            for i in range(n):
+                q.potential(rr, phis[i % NSETS])
+            b.record()
+            torch.cuda.synchronize()
+            diag["%s_%s_ms" % (interp, prec)] = a.elapsed_time(b) / n
+            q.close()
+    out["interp_readings"] = diag
+    return out
+
+
+
+
 def cufft_half_spectrum(torch, octant, dev, dtype):
     """The (2N)^3 Green spectrum in torch.fft.rfftn's half layout (P, P, N+1)
     from the library's real even octant ((N+1)^3, [kz][ky][kx])."""

@@ -774,8 +774,14 @@ cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, int geom, const nm_
 
 template <typename T>
 nm_status enqueue_restrict(nm_plan_t p, const void* rho, cudaStream_t s) {
-    cudaError_t e = run_restrict_chain<T>((const T*)rho, (T*)p->restr, p->L, p->N, s);
-    if (e != cudaSuccess) return cuda_fail(e, "restriction");
+    const int L = p->L, N = p->N;
+    const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
+    for (int m = L - 2; m >= 0; --m) {
+        const T* child = (const T*)rho + (size_t)(m + 1) * N3;
+        const T* rchild = (m + 1 < L - 1) ? (const T*)p->restr + (size_t)(m + 1) * h3 : nullptr;
+        cudaError_t e = run_restrict<T>(child, rchild, (T*)p->restr + (size_t)m * h3, N, s);
+        if (e != cudaSuccess) return cuda_fail(e, "restriction");
+    }
     return NM_OK;
 }
 

@@ -63,10 +63,6 @@ template <typename TIN>
 cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* restr_out, int N,
                          cudaStream_t s);
 
-// The whole restriction sweep (levels L-2 .. 0) in one cooperative launch.
-template <typename TIN>
-cudaError_t run_restrict_chain(const TIN* rho, TIN* restr, int L, int N, cudaStream_t s);
-
 // Final assembly (Eq. 14 / Eqs. 15, B.1-B.2) into phi (double).
 template <typename T> struct AssembleArgs {
     const T* base[16];     // per level: Phi^n (original) or Phi^n_hole (dipole), N^3

@@ -1,6 +1,4 @@
 // support.cu -- restriction, Green spectrum and final assembly kernels.
-#include <cooperative_groups.h>
-
 #include "../../include/nm.h"
 #include "internal.h"
 
@@ -108,132 +106,6 @@ cudaError_t run_restrict(const TIN* rho_child, const TIN* restr_child, TIN* rest
 }
 template cudaError_t run_restrict<float>(const float*, const float*, float*, int, cudaStream_t);
 template cudaError_t run_restrict<double>(const double*, const double*, double*, int, cudaStream_t);
-
-// The whole restriction sweep in one cooperative launch: level m = L-2 down
-// to 0, each step reading the step before it, with a grid-wide barrier in
-// between (all CTAs of a cooperative launch are resident together, so the
-// barrier always completes).  The restricted values of the previous step are
-// read through L2 (ld.global.cg): another SM wrote them in this launch.
-template <typename TIN> struct RestrictChain {
-    const TIN* rho;   // L N^3
-    TIN* restr;       // (L-1) (N/2)^3
-    int L, lgN;
-};
-
-template <typename TIN, bool VEC>
-__global__ void __launch_bounds__(256) k_restrict_chain(const __grid_constant__ RestrictChain<TIN> a) {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    const int lgN = a.lgN, N = 1 << lgN, h = N / 2, q = N / 4, lgh = lgN - 1;
-    const size_t N3 = (size_t)1 << (3 * lgN), h3 = N3 / 8;
-    for (int m = a.L - 2; m >= 0; --m) {
-        const TIN* child = a.rho + (size_t)(m + 1) * N3;
-        const TIN* rchild = m + 1 < a.L - 1 ? a.restr + (size_t)(m + 1) * h3 : nullptr;
-        TIN* out = a.restr + (size_t)m * h3;
-        if (VEC) {
-            const int n = (h * h * h) / 2;
-            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-                const int c = 2 * (i & (h / 2 - 1)), b = (i >> (lgh - 1)) & (h - 1), z0 = i >> (2 * lgh - 1);
-                TIN s0 = TIN(0), s1 = TIN(0);
-#pragma unroll
-                for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                    for (int dy = 0; dy < 2; ++dy) {
-                        const int z = 2 * z0 + dz, y = 2 * b + dy, x = 2 * c;
-                        const bool cov = rchild && (unsigned)(z - q) < (unsigned)h &&
-                                         (unsigned)(y - q) < (unsigned)h && (unsigned)(x - q) < (unsigned)h;
-                        TIN w[4];
-                        if (cov) {
-                            const TIN* p = rchild + ((size_t)(z - q) * h + (y - q)) * h + (x - q);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) w[k] = __ldcg(p + k);
-                        } else {
-                            Vec4In<TIN>::load(child + ((size_t)z * N + y) * N + x, w);
-                        }
-                        s0 += w[0] + w[1];
-                        s1 += w[2] + w[3];
-                    }
-                out[2 * i] = s0 * TIN(0.125);
-                out[2 * i + 1] = s1 * TIN(0.125);
-            }
-        } else {
-            const int n = h * h * h;
-            for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-                const int c = i & (h - 1), b = (i >> lgh) & (h - 1), z0 = i >> (2 * lgh);
-                TIN s = TIN(0);
-#pragma unroll
-                for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 2; ++dx) {
-                            const int z = 2 * z0 + dz, y = 2 * b + dy, x = 2 * c + dx;
-                            const bool cov = rchild && (unsigned)(z - q) < (unsigned)h &&
-                                             (unsigned)(y - q) < (unsigned)h && (unsigned)(x - q) < (unsigned)h;
-                            s += cov ? __ldcg(rchild + ((size_t)(z - q) * h + (y - q)) * h + (x - q))
-                                     : child[((size_t)z * N + y) * N + x];
-                        }
-                out[i] = s * TIN(0.125);
-            }
-        }
-        if (m > 0) grid.sync();
-    }
-}
-
-// Occupancy-sized grid of a cooperative kernel (resident CTAs per SM x SMs),
-// at most `want` CTAs; 0 when the kernel cannot be resident at all.
-template <typename K>
-static int coop_grid(K kernel, int threads, int want) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess) return 0;
-    const int g = occ * sm_count();
-    return g < want ? g : want;
-}
-
-template <typename K, typename A>
-static cudaError_t launch_coop(K kernel, int grid, int threads, const A& args, cudaStream_t s) {
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args);
-}
-
-template <typename TIN>
-cudaError_t run_restrict_chain(const TIN* rho, TIN* restr, int L, int N, cudaStream_t s) {
-    if (L < 2) return cudaSuccess;
-    const RestrictChain<TIN> a{rho, restr, L, ilog2(N)};
-    const bool vec = N >= 16 && ((uintptr_t)rho & 15) == 0 && ((uintptr_t)restr & 15) == 0;
-    const int n = (N / 2) * (N / 2) * (N / 2) / (vec ? 2 : 1);
-    const int want = (n + 255) / 256;
-    ProfScope ps(sizeof(TIN) == 4 ? "restrict_f32" : "restrict_f64", L - 1, s);
-    static const int g_vec = coop_grid(k_restrict_chain<TIN, true>, 256, 1 << 30);
-    static const int g_sc = coop_grid(k_restrict_chain<TIN, false>, 256, 1 << 30);
-    const int g = vec ? g_vec : g_sc;
-    if (g <= 0) {
-        // not launchable cooperatively: one launch per level
-        for (int m = L - 2; m >= 0; --m) {
-            const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
-            cudaError_t e = run_restrict<TIN>(rho + (size_t)(m + 1) * N3,
-                                              m + 1 < L - 1 ? restr + (size_t)(m + 1) * h3 : nullptr,
-                                              restr + (size_t)m * h3, N, s);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaSuccess;
-    }
-    cudaError_t e = vec ? launch_coop(k_restrict_chain<TIN, true>, g < want ? g : want, 256, a, s)
-                        : launch_coop(k_restrict_chain<TIN, false>, g < want ? g : want, 256, a, s);
-    count_launches(1);
-    return e;
-}
-template cudaError_t run_restrict_chain<float>(const float*, float*, int, int, cudaStream_t);
-template cudaError_t run_restrict_chain<double>(const double*, double*, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------- Green spectrum
 // The unit-cell kernel of Eq. 10 (1/|d| for integer offsets d != 0, the
@@ -605,40 +477,6 @@ cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
 template cudaError_t run_assemble<float>(const AssembleArgs<float>&, cudaStream_t);
 template cudaError_t run_assemble<double>(const AssembleArgs<double>&, cudaStream_t);
 
-// The carried interpolation's steps n = 1 .. L-2 in one cooperative launch,
-// a grid-wide barrier between steps (step n reads step n-1, written by other
-// SMs in this launch: through L2, ld.global.cg).
-template <typename T> struct CarryChain {
-    CarryArgs<T> step[16];
-    int steps;
-};
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_carry_chain(const __grid_constant__ CarryChain<T> a) {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    for (int k = 0; k < a.steps; ++k) {
-        const CarryArgs<T>& c = a.step[k];
-        const int N = c.N, nc = N / 2 + 2, o = N / 4 - 1;
-        const size_t total = (size_t)nc * nc * nc;
-        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-             i += (size_t)gridDim.x * blockDim.x) {
-            const int x = (int)(i % nc) + o, y = (int)((i / nc) % nc) + o, z = (int)(i / ((size_t)nc * nc)) + o;
-            int cz, sz, cy, sy, cx, sx;
-            diag_axis(N, z, cz, sz);
-            diag_axis(N, y, cy, sy);
-            diag_axis(N, x, cx, sx);
-            const int po = c.prev_origin, pE = c.prev_extent;
-            const T near = __ldcg(c.prev + ((size_t)(cz - po) * pE + (cy - po)) * pE + (cx - po));
-            const T diag = __ldcg(c.prev + ((size_t)(cz + sz - po) * pE + (cy + sy - po)) * pE + (cx + sx - po));
-            const int ho = c.hole_origin, hE = c.hole_extent;
-            const T hv = c.hole[((size_t)(z - ho) * hE + (y - ho)) * hE + (x - ho)];
-            c.out[i] = (T(0.75) * near + T(0.25) * diag) + hv;
-        }
-        if (k + 1 < a.steps) grid.sync();
-    }
-}
-
 template <typename T>
 cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStream_t s) {
     if (interp == NM_INTERP_DIAGONAL) {
@@ -647,9 +485,8 @@ cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStr
         const int N = a.N;
         const size_t nc = N / 2 + 2, nc3 = nc * nc * nc;
         a.diag = 1;
-        CarryChain<T> ch{};
         for (int n = 1; n + 1 < a.levels; ++n) {
-            CarryArgs<T>& c = ch.step[ch.steps++];
+            CarryArgs<T> c{};
             c.prev = a.interp[n - 1];
             c.prev_origin = a.interp_origin[n - 1];
             c.prev_extent = a.interp_extent[n - 1];
@@ -658,23 +495,11 @@ cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStr
             c.hole_extent = a.interp_extent[n];
             c.out = carry + (size_t)(n - 1) * nc3;
             c.N = N;
+            cudaError_t e = run_carry<T>(c, s);
+            if (e != cudaSuccess) return e;
             a.interp[n] = c.out;
             a.interp_origin[n] = N / 4 - 1;
             a.interp_extent[n] = (int)nc;
-        }
-        if (ch.steps > 0) {
-            static const int g = coop_grid(k_carry_chain<T>, 256, 1 << 30);
-            const int want = (int)((nc3 + 255) / 256);
-            cudaError_t e;
-            if (g > 0) {
-                ProfScope ps(sizeof(T) == 4 ? "carry_f32" : "carry_f64", ch.steps, s);
-                e = launch_coop(k_carry_chain<T>, g < want ? g : want, 256, ch, s);
-                count_launches(1);
-            } else {
-                e = cudaSuccess;
-                for (int k = 0; k < ch.steps && e == cudaSuccess; ++k) e = run_carry<T>(ch.step[k], s);
-            }
-            if (e != cudaSuccess) return e;
         }
     }
     return run_assemble<T>(a, s);

@@ -1,0 +1,43 @@
+"""bench.py's contract on the CPU: the module imports, every mode's entry
+point exists, and the reference arm (the oracle on the host) prints one JSON
+line with the keys the driver reads."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_entry_points_exist():
+    for name in ("ours", "batch_mode", "serve_mode", "accel_mode", "table_mode", "reference_arm",
+                 "cpu_baseline", "accel_rates", "dipole_rates", "cufft_baseline", "cufft_level_convolutions",
+                 "oracle_solve_timed", "oracle_pool"):
+        assert callable(getattr(bench, name)), name
+
+
+def test_reference_arm_prints_one_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                          "--levels", "2", "--N", "16"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "solves/s" and d["value"] > 0
+    for k in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_solve_timed_matches_oracle():
+    import numpy as np
+    import oracle
+    from paper_2301_06763_gb300 import workloads as wl
+    w = wl.config_small()
+    rho = w.rho()
+    phi, t = bench.oracle_solve_timed(rho, w.N, w.dx0)
+    assert t > 0
+    assert np.max(np.abs(phi - oracle.solve(rho, w.N, w.dx0))) == 0.0
