@@ -29,9 +29,10 @@ _ES = {"fp32": 4, "fp64": 8}
 
 
 class Request:
-    def __init__(self, rid, levels, N, dx0, rho, arrival=0.0, G=1.0, keep_result=True):
+    def __init__(self, rid, levels, N, dx0, rho, arrival=0.0, G=1.0, keep_result=True, method="original"):
         self.rid = rid
         self.levels, self.N, self.dx0, self.G = int(levels), int(N), float(dx0), float(G)
+        self.method = method            # "original", "dipole", "dipole3" or "dipole3_ds"
         self.rho = rho                  # host (levels, N, N, N): numpy array or (pinned) CPU tensor
         self.arrival = float(arrival)   # wall-clock seconds (perf_counter) of arrival
         self.keep_result = keep_result
@@ -58,7 +59,7 @@ class Server:
         self.max_batch = int(max_batch)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         self.free = list(range(slots))
-        self.pool = collections.OrderedDict()   # (L, N, dx0, G) -> [Plan], LRU order
+        self.pool = collections.OrderedDict()   # (L, N, dx0, G, method) -> [Plan], LRU order
         self.pool_bytes = 0
         self.queue = collections.deque()
         self.inflight = []
@@ -74,11 +75,11 @@ class Server:
         cells = r.levels * r.N ** 3
         b = cells * (_ES[self.precision] + 8)
         if with_plan:
-            b += nm.footprint_bytes(r.levels, r.N, r.dx0, r.G, self.precision)
+            b += nm.footprint_bytes(r.levels, r.N, r.dx0, r.G, self.precision, r.method)
         return b
 
     def _take_plan(self, r):
-        key = (r.levels, r.N, r.dx0, r.G)
+        key = (r.levels, r.N, r.dx0, r.G, r.method)
         plans = self.pool.get(key)
         if plans:
             p = plans.pop()
@@ -112,7 +113,7 @@ class Server:
                     if r.keep_result:
                         r.result = r._phi_host.numpy()
                     self.used -= r.bytes
-                    key = (r.levels, r.N, r.dx0, r.G)
+                    key = (r.levels, r.N, r.dx0, r.G, r.method)
                     self.pool.setdefault(key, []).append(r._plan)
                     self.pool.move_to_end(key)
                     self.pool_bytes += r._plan.workspace_bytes()
@@ -141,19 +142,19 @@ class Server:
                 self.queue.popleft()
                 r.error = "footprint %d bytes exceeds the HBM budget %d" % (need, self.budget)
                 if plan is not None:
-                    self.pool.setdefault((r.levels, r.N, r.dx0, r.G), []).append(plan)
+                    self.pool.setdefault((r.levels, r.N, r.dx0, r.G, r.method), []).append(plan)
                     self.pool_bytes += plan.workspace_bytes()
                 self.failed.append(r)
                 continue
             if not self._evict_until(need):
                 if plan is not None:
-                    self.pool.setdefault((r.levels, r.N, r.dx0, r.G), []).append(plan)
+                    self.pool.setdefault((r.levels, r.N, r.dx0, r.G, r.method), []).append(plan)
                     self.pool_bytes += plan.workspace_bytes()
                 break
             self.queue.popleft()
             try:
                 if plan is None:
-                    plan = nm.Plan(r.levels, r.N, r.dx0, r.G, precision=self.precision)
+                    plan = nm.Plan(r.levels, r.N, r.dx0, r.G, precision=self.precision, method=r.method)
                     need = self.request_bytes(r, with_plan=False) + plan.workspace_bytes()
             except Exception as e:          # invalid shape or allocation failure
                 r.error = str(e)

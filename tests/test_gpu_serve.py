@@ -69,3 +69,25 @@ def test_bad_requests_fail_alone():
     for r in good:
         assert np.array_equal(r.result, solo(r))
     srv.close()
+
+
+def test_mixed_methods_alone_and_in_the_mix():
+    # requests naming the dipole schemes ride in the same batches as plain
+    # ones; each result equals the same request solved alone
+    import torch
+    from paper_2301_06763_gb300.serve import Request, Server, run_stream
+    m = nm()
+    methods = ["original", "dipole", "dipole3", "dipole3_ds", "dipole3"]
+    reqs = []
+    for i in range(15):
+        L, N = [(3, 8), (4, 16), (3, 16)][i % 3]
+        rho = wl.random_density(500 + i, L, N).astype(np.float32)
+        reqs.append(Request(i, L, N, 1.0 / N, rho, arrival=i * 0.0003, method=methods[i % len(methods)]))
+    srv = Server(hbm_budget_bytes=4 << 30, slots=3, precision="fp32", max_batch=4)
+    run_stream(srv, reqs)
+    assert len(srv.completed) == 15 and not srv.failed
+    for r in reqs:
+        with m.Plan(r.levels, r.N, r.dx0, precision="fp32", method=r.method) as p:
+            ref = p.potential(torch.from_numpy(r.rho).cuda()).cpu().numpy()
+        assert np.array_equal(r.result, ref), r.method
+    srv.close()
