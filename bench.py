@@ -815,11 +815,33 @@ def table_mode(args):
         t1 = sum(oracle_solve_timed(rhos[i], meshes[i].N, meshes[i].dx0, None)[1] for i in sub)
         ta = sum(oracle_solve_timed(rhos[i], meshes[i].N, meshes[i].dx0, pool)[1] for i in sub)
         scale = len(meshes) / len(sub)
+        # the paper's runtime setting (Sect. 6 / Sect. 6's GPU runs): the oblate
+        # ellipsoid on 8 levels of 128^3, timing only
+        w = wl.config_paper_ellipsoid(N=128, levels=8)
+        rho = w.rho()
+        paper_row = {"config": "paper setting: ellipsoid 8x128^3", "gpu_fp64_ms": gpu_ms(w, rho, "fp64", reps=5),
+                     "gpu_fp32_ms": gpu_ms(w, rho, "fp32"), "cufft_fp32_ms": cufft_ms(w, rho, "fp32"),
+                     "cufft_fp64_ms": cufft_ms(w, rho, "fp64", reps=3)}
+        _, ta = oracle_solve_timed(rho, w.N, w.dx0, pool)
+        paper_row["oracle_all_cores_ms"] = ta * 1e3
         rows.append({"config": "4: batch of 64", "gpu_fp32_ms": batch_ms, "gpu_fp64_ms": fp64_ms,
                      "cufft_fp32_ms": cuf, "oracle_1core_ms": t1 * scale * 1e3,
                      "oracle_all_cores_ms": ta * scale * 1e3,
                      "note": "GPU FP32 = one nm_batch_potential; FP64 and cuFFT = the 64 meshes one by one; "
                              "oracle on 8 of the 64 meshes, scaled by 8"})
+        # serving requests: the oracle on a sample of the stream's small meshes
+        rng = np.random.default_rng(0)
+        sample, t1 = [], 0.0
+        for i in range(8):
+            N = int(rng.choice([32, 64]))
+            L = int(rng.integers(3, 11))
+            ws = wl.Workload("serve-%d" % N, L, N, 1.0 / N, wl.random_plummers(rng, L, N))
+            r = ws.rho()
+            t1 += oracle_solve_timed(r, N, ws.dx0, pool)[1]
+            sample.append("%dx%d" % (L, N))
+        rows.append({"config": "5: serving requests (sample)", "oracle_all_cores_ms_per_request": t1 / 8 * 1e3,
+                     "sample": sample, "note": "8 requests with N in {32, 64} from the request distribution"})
+        rows.append(paper_row)
     finally:
         pool.shutdown()
     print(json.dumps({"mode": "table", "host_cores": os.cpu_count(), "oracle_workers": workers,
