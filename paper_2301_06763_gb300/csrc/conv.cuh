@@ -188,6 +188,84 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
     }
 }
 
+// Pass 1 as a persistent pipeline (level grids whose pairs are a level's full
+// and hole fields, or a full field alone; density 16-byte aligned; P >= 64).
+// A tile is the LINES consecutive density rows that one round of the CTA
+// transforms; each CTA walks tiles blockIdx.x, + gridDim.x, ... across all
+// pairs and fetches tile k+1 into the other half of a two-tile staging buffer
+// with asynchronous 16-byte copies (cp.async, completion by wait_group, which
+// the hardware resolves) while it transforms tile k, so the density loads
+// overlap the transforms instead of preceding them.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <typename T, int P, int E>
+__global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvArgs<T> a, int npairs) {
+    using G = Geo<P, E, 0>;
+    constexpr int TPL = P / E, LINES = 256 / TPL, NIN = G::NIN;
+    constexpr int TILE = LINES * NIN;                 // density values per tile
+    constexpr int TILES = NIN * NIN / LINES;          // tiles per pair
+    constexpr int VEC = 16 / sizeof(T);
+    static_assert((NIN * NIN) % LINES == 0 && TILE % (256 * VEC) == 0, "tile shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* sm_lines = sm_tw + P;
+    T* stage = reinterpret_cast<T*>(sm_lines + LINES * (P + P / E));   // [2][TILE]
+    load_twiddles(sm_tw, a.tw, P);
+    const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
+    const int total = npairs * TILES;
+    auto issue = [&](int t, int b) {
+        const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
+        const T* src = (const T*)a.pair[pr].src[0].rho + (size_t)row0 * NIN;
+        T* dst = stage + b * TILE;
+#pragma unroll
+        for (int i = threadIdx.x * VEC; i < TILE; i += 256 * VEC) cp_async16(dst + i, src + i);
+    };
+    int t = blockIdx.x;
+    if (t < total) issue(t, 0);
+    cp_async_commit();
+    for (int k = 0; t < total; ++k, t += gridDim.x) {
+        if (t + (int)gridDim.x < total) issue(t + gridDim.x, (k + 1) & 1);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
+        const PairDesc<T>& d = a.pair[pr];
+        const T s0 = (T)d.src[0].scale, s1 = (T)d.src[1].scale;
+        const int row = row0 + line;
+        const int zi = row / NIN, yi = row % NIN;
+        const int q = NIN / 4, h = NIN / 2;
+        const bool row_cov = (unsigned)(zi - q) < (unsigned)h && (unsigned)(yi - q) < (unsigned)h;
+        const bool hole = d.src[1].mode == SRC_HOLE;
+        const T* st = stage + (k & 1) * TILE + line * NIN;
+        cpx<T> v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = {T(0), T(0)};
+            if (G::live(r)) {
+                const int xi = j + r * (P / E);
+                const T val = st[xi];
+                const bool cov = row_cov && (unsigned)(xi - q) < (unsigned)h;
+                T full = val;
+                if (cov && d.src[0].restr) full = ((const T*)d.src[0].restr)[((size_t)(zi - q) * h + (yi - q)) * h + (xi - q)];
+                v[r].re = full * s0;
+                v[r].im = (hole && !cov) ? val * s1 : T(0);
+            }
+        }
+        fft_line<T, P, E, false>(v, j, sm_tw,
+                                 LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
+        cpx<T>* out = d.work + ((size_t)zi * P + yi) * P;
+#pragma unroll
+        for (int s = 0; s < E; ++s) out[out_index<P, E>(j, s)] = v[s];
+        __syncthreads();   // this half of the stage and the line scratch are free again
+    }
+}
+
 // ---------------------------------------------------------------- passes 2, 4
 template <typename T, int P, int E, int TX, bool INV, int GM>
 __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ ConvArgs<T> a) {
@@ -312,6 +390,63 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
                 store_out<T, P>(d.dst[1], z, y, e, v[s].im);
             }
         }
+    }
+}
+
+// Pass 5 as a persistent pipeline (float, P >= 128): tiles of LINES
+// consecutive work rows, the next one fetched by cp.async into the other of
+// two buffers while the current one is transformed.  Each buffer is large
+// enough to serve, once its rows are in registers, as the transform's
+// exchange space for the same tile.
+template <typename T, int P, int E>
+__global__ void __launch_bounds__(256) k_xinv_pipe(const __grid_constant__ ConvArgs<T> a, int npairs) {
+    constexpr int TPL = P / E, LINES = 256 / TPL, HALF = P / 2;
+    constexpr int ROWS = HALF * HALF;                 // output rows per pair
+    constexpr int TILES = ROWS / LINES;
+    constexpr int BUF = LINES * (P + P / E);          // complex values per buffer
+    constexpr int TILE = LINES * P;                   // complex values fetched per tile
+    constexpr int CH = TILE * (int)sizeof(cpx<T>) / 16;
+    static_assert(ROWS % LINES == 0 && HALF % LINES == 0 && CH % 256 == 0, "tile shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* buf = sm_tw + P;                          // [2][BUF]
+    load_twiddles(sm_tw, a.tw, P);
+    const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
+    const int total = npairs * TILES;
+    auto issue = [&](int t, int b) {
+        const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
+        const int z = row0 / HALF, y = row0 % HALF;   // the tile's rows share z
+        const char* src = (const char*)(a.pair[pr].work + ((size_t)z * P + y) * P);
+        char* dst = (char*)(buf + b * BUF);
+#pragma unroll
+        for (int i = threadIdx.x; i < CH; i += 256) cp_async16(dst + 16 * i, src + 16 * (size_t)i);
+    };
+    int t = blockIdx.x;
+    if (t < total) issue(t, 0);
+    cp_async_commit();
+    for (int k = 0; t < total; ++k, t += gridDim.x) {
+        if (t + (int)gridDim.x < total) issue(t + gridDim.x, (k + 1) & 1);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int pr = t / TILES, row = (t - pr * TILES) * LINES + line;
+        const int z = row / HALF, y = row % HALF;
+        const PairDesc<T>& d = a.pair[pr];
+        cpx<T>* b = buf + (k & 1) * BUF;
+        cpx<T> v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) v[r] = b[line * P + j + r * (P / E)];
+        __syncthreads();
+        fft_line<T, P, E, true>(v, j, sm_tw, LineView<T, 1, true, Log2E<E>::value>{b + line * (P + P / E)});
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            const int e = out_index<P, E>(j, s);
+            if (e < HALF) {
+                store_out<T, P>(d.dst[0], z, y, e, v[s].re);
+                store_out<T, P>(d.dst[1], z, y, e, v[s].im);
+            }
+        }
+        __syncthreads();   // the buffer is free for the fetch two tiles ahead
     }
 }
 

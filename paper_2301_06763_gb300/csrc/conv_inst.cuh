@@ -129,7 +129,34 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
     {
         snprintf(nm_, sizeof nm_, "xfwd%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_xfwd<T, T, P, E, GM><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        bool pipe = false;
+        if constexpr (GM == 0 && P >= 64 && E == 16) {
+            // every pair a level's full field with its hole field (or alone),
+            // on a 16-byte aligned density
+            pipe = true;
+            for (int i = 0; i < np && pipe; ++i) {
+                const PairDesc<T>& d = a.pair[i];
+                pipe = d.src[0].mode == SRC_FULL && ((uintptr_t)d.src[0].rho & 15) == 0 &&
+                       (d.src[1].mode == SRC_NONE || (d.src[1].mode == SRC_HOLE && d.src[1].rho == d.src[0].rho));
+            }
+            if (pipe) {
+                constexpr int TILE = LINES * Gm::NIN;
+                const size_t sm_p = sm_x + 2 * (size_t)TILE * sizeof(T);
+                static int occ = -1;
+                static const cudaError_t prep_p = [&]() {
+                    cudaError_t e = prep_kernel(k_xfwd_pipe<T, P, E>, sm_p);
+                    if (e == cudaSuccess)
+                        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_pipe<T, P, E>, 256, sm_p);
+                    return e;
+                }();
+                if (prep_p != cudaSuccess) return prep_p;
+                const int tiles = np * (rows_in / LINES);
+                int grid = (occ > 0 ? occ : 1) * sm_count();
+                if (grid > tiles) grid = tiles;
+                k_xfwd_pipe<T, P, E><<<grid, 256, sm_p, s>>>(a, np);
+            }
+        }
+        if (!pipe) k_xfwd<T, T, P, E, GM><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "yfwd%s_%s_P%d", geo, tag, P);
@@ -158,7 +185,24 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
     {
         snprintf(nm_, sizeof nm_, "xinv%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        k_xinv<T, P, E, GM><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        bool pipe = false;
+        if constexpr (sizeof(T) == 4 && P >= 128 && E == 16) {
+            pipe = true;
+            const size_t sm_p = (size_t)P * c + 2 * (size_t)LINES * (P + P / E) * c;
+            static int occ = -1;
+            static const cudaError_t prep_p = [&]() {
+                cudaError_t e = prep_kernel(k_xinv_pipe<T, P, E>, sm_p);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_pipe<T, P, E>, 256, sm_p);
+                return e;
+            }();
+            if (prep_p != cudaSuccess) return prep_p;
+            const int tiles = np * (rows_out / LINES);
+            int grid = (occ > 0 ? occ : 1) * sm_count();
+            if (grid > tiles) grid = tiles;
+            k_xinv_pipe<T, P, E><<<grid, 256, sm_p, s>>>(a, np);
+        }
+        if (!pipe) k_xinv<T, P, E, GM><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     count_launches(5);
     return cudaGetLastError();
