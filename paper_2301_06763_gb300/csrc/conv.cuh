@@ -393,63 +393,6 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
     }
 }
 
-// Pass 5 as a persistent pipeline (float, P >= 128): tiles of LINES
-// consecutive work rows, the next one fetched by cp.async into the other of
-// two buffers while the current one is transformed.  Each buffer is large
-// enough to serve, once its rows are in registers, as the transform's
-// exchange space for the same tile.
-template <typename T, int P, int E>
-__global__ void __launch_bounds__(256) k_xinv_pipe(const __grid_constant__ ConvArgs<T> a, int npairs) {
-    constexpr int TPL = P / E, LINES = 256 / TPL, HALF = P / 2;
-    constexpr int ROWS = HALF * HALF;                 // output rows per pair
-    constexpr int TILES = ROWS / LINES;
-    constexpr int BUF = LINES * (P + P / E);          // complex values per buffer
-    constexpr int TILE = LINES * P;                   // complex values fetched per tile
-    constexpr int CH = TILE * (int)sizeof(cpx<T>) / 16;
-    static_assert(ROWS % LINES == 0 && HALF % LINES == 0 && CH % 256 == 0, "tile shape");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
-    cpx<T>* buf = sm_tw + P;                          // [2][BUF]
-    load_twiddles(sm_tw, a.tw, P);
-    const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
-    const int total = npairs * TILES;
-    auto issue = [&](int t, int b) {
-        const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
-        const int z = row0 / HALF, y = row0 % HALF;   // the tile's rows share z
-        const char* src = (const char*)(a.pair[pr].work + ((size_t)z * P + y) * P);
-        char* dst = (char*)(buf + b * BUF);
-#pragma unroll
-        for (int i = threadIdx.x; i < CH; i += 256) cp_async16(dst + 16 * i, src + 16 * (size_t)i);
-    };
-    int t = blockIdx.x;
-    if (t < total) issue(t, 0);
-    cp_async_commit();
-    for (int k = 0; t < total; ++k, t += gridDim.x) {
-        if (t + (int)gridDim.x < total) issue(t + gridDim.x, (k + 1) & 1);
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        const int pr = t / TILES, row = (t - pr * TILES) * LINES + line;
-        const int z = row / HALF, y = row % HALF;
-        const PairDesc<T>& d = a.pair[pr];
-        cpx<T>* b = buf + (k & 1) * BUF;
-        cpx<T> v[E];
-#pragma unroll
-        for (int r = 0; r < E; ++r) v[r] = b[line * P + j + r * (P / E)];
-        __syncthreads();
-        fft_line<T, P, E, true>(v, j, sm_tw, LineView<T, 1, true, Log2E<E>::value>{b + line * (P + P / E)});
-#pragma unroll
-        for (int s = 0; s < E; ++s) {
-            const int e = out_index<P, E>(j, s);
-            if (e < HALF) {
-                store_out<T, P>(d.dst[0], z, y, e, v[s].re);
-                store_out<T, P>(d.dst[1], z, y, e, v[s].im);
-            }
-        }
-        __syncthreads();   // the buffer is free for the fetch two tiles ahead
-    }
-}
-
 // Column tile width of the strided passes: at most the requested width W,
 // at most 1024 threads, never wider than a row of the domain.
 template <int P, int E, int W> struct Tile {

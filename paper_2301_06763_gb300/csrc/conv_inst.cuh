@@ -166,16 +166,15 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
     {
         snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
+        bool done = false;
         if constexpr (GM == 0) {
             if (tma) {
                 cudaError_t e = zseam_tma<T, P, E, TX>(a, np, s);
                 if (e != cudaSuccess) return e;
-            } else {
-                k_zseam<T, P, E, TX, GM><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
+                done = true;
             }
-        } else {
-            k_zseam<T, P, E, TX, GM><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
         }
+        if (!done) k_zseam<T, P, E, TX, GM><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "yinv%s_%s_P%d", geo, tag, P);
@@ -185,24 +184,7 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
     {
         snprintf(nm_, sizeof nm_, "xinv%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
-        bool pipe = false;
-        if constexpr (sizeof(T) == 4 && P >= 128 && E == 16) {
-            pipe = true;
-            const size_t sm_p = (size_t)P * c + 2 * (size_t)LINES * (P + P / E) * c;
-            static int occ = -1;
-            static const cudaError_t prep_p = [&]() {
-                cudaError_t e = prep_kernel(k_xinv_pipe<T, P, E>, sm_p);
-                if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xinv_pipe<T, P, E>, 256, sm_p);
-                return e;
-            }();
-            if (prep_p != cudaSuccess) return prep_p;
-            const int tiles = np * (rows_out / LINES);
-            int grid = (occ > 0 ? occ : 1) * sm_count();
-            if (grid > tiles) grid = tiles;
-            k_xinv_pipe<T, P, E><<<grid, 256, sm_p, s>>>(a, np);
-        }
-        if (!pipe) k_xinv<T, P, E, GM><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        k_xinv<T, P, E, GM><<<dim3((rows_out + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     count_launches(5);
     return cudaGetLastError();
