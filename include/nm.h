@@ -105,7 +105,7 @@ typedef struct {
                         stencil of Fig. 6):
                         NM_INTERP_TRILINEAR: tensor-product linear from each
                           level k straight to every finer level n;
-                        NM_INTERP_DIAGONAL: the two-point rule of Eqs. 3-6
+                        NM_INTERP_DIAGONAL (default): the two-point rule of Eqs. 3-6
                           (3/4 of the nearest coarse value plus 1/4 of its
                           diagonal neighbour towards the fine centre), carried
                           one level at a time: carry_n = D(carry_{n-1} +
@@ -115,7 +115,8 @@ typedef struct {
 } nm_options;
 
 /* Fill `opt` with the defaults used by nm_plan: G = 1, NM_FP64, original
- * method, trilinear interpolation.  No device work. */
+ * method, NM_INTERP_DIAGONAL (the Eqs. 3-6 rule, the reading that reproduces
+ * the paper's acceleration errors).  No device work. */
 nm_status nm_default_options(int levels, int N, double dx0, nm_options* opt);
 
 /* Create a plan for one nested mesh on the current CUDA device: validates the
