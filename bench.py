@@ -515,16 +515,24 @@ def ours(args):
     dev64_ms = max_over_ranks(torch, dist, dev64_ms)
     clk = clocks.stop()
 
-    # end to end through the host-buffer entry point (H2D + solve + D2H per step)
+    # end to end through the host-buffer entry points (H2D + solve + D2H per
+    # step, from and to page-locked host memory): the pipelined one, whose
+    # copies overlap the neighbouring steps' solves, and one call per step
     h_rho = torch.from_numpy(rho.astype(np.float32)).pin_memory()
     h_phi = torch.empty(rho.shape, dtype=torch.float64).pin_memory()
+    p32.potential_host_many([h_rho] * 3, [h_phi] * 3)
     p32.potential_host(h_rho.numpy(), h_phi.numpy())
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    p32.potential_host_many([h_rho] * args.steps, [h_phi] * args.steps)
+    e2e_s = max_over_ranks(torch, dist, time.perf_counter() - t0)
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         p32.potential_host(h_rho.numpy(), h_phi.numpy())
-    e2e_s = max_over_ranks(torch, dist, time.perf_counter() - t0)
+    e2e_sync_s = max_over_ranks(torch, dist, time.perf_counter() - t0)
 
     # per-kernel event timing (instrumented repeat of the FP32 timed loop)
     nm.profile_enable(True)
@@ -591,7 +599,9 @@ def ours(args):
                 "solve_gbs": solve_bytes / (ms_step * 1e-3) / 1e9,
                 "frac": solve_bytes / (ms_step * 1e-3) / 1e9 / peak},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
-                "h2d_bytes_per_step": int(rho.size * 4), "d2h_bytes_per_step": int(rho.size * 8)},
+                "h2d_bytes_per_step": int(rho.size * 4), "d2h_bytes_per_step": int(rho.size * 8),
+                "api": "nm_potential_host_many (copies overlapped with the neighbouring solves)",
+                "one_call_per_step": world * args.steps / e2e_sync_s},
         "gpu_launches": int(launches),
         "roofline": roof,
         "kernels": kernel_table,

@@ -174,6 +174,15 @@ nm_status nm_acceleration_ex(nm_plan_t plan, const double* phi, double* g, int c
 /* Same result from HOST buffers: copies rho to the device, solves, copies phi
  * back, all on `stream`, and waits for the stream before returning.  Host
  * buffers in pinned memory give asynchronous copies. */
+/* n solves from HOST buffers, pipelined: the upload of solve i+1 and the
+ * download of solve i-1 run on two copy streams of the plan while solve i runs
+ * on `stream` (two device staging sets, allocated on first use and counted in
+ * nm_workspace_bytes).  rho_host[i] and phi_host[i] as for nm_potential_host;
+ * page-locked host memory lets the copies overlap.  Synchronous: returns when
+ * every phi_host[i] is written.  Calls on one plan must not overlap. */
+nm_status nm_potential_host_many(nm_plan_t plan, int n, const void* const* rho_host, double* const* phi_host,
+                                 void* stream);
+
 nm_status nm_potential_host(nm_plan_t plan, const void* rho_host, double* phi_host,
                             void* stream);
 

@@ -283,6 +283,10 @@ struct nm_plan_s {
     void* red = nullptr;              // (L-2) * N^3 reduced quadrupled grids or Eq. B.6 sums
     void* h_rho = nullptr;            // staging for nm_potential_host
     double* h_phi = nullptr;
+    void* h_rho2[2] = {nullptr, nullptr};       // double-buffered staging of nm_potential_host_many
+    double* h_phi2[2] = {nullptr, nullptr};
+    cudaStream_t s_in = nullptr, s_out = nullptr;   // its copy streams
+    cudaEvent_t ev_in[2] = {}, ev_solved[2] = {}, ev_out[2] = {};
     size_t ws_bytes = 0;
     Spectrum* spec = nullptr;
     Spectrum* spec_dbl = nullptr;
@@ -318,6 +322,19 @@ void plan_free_buffers(nm_plan_t p) {
     cudaFree(p->red);
     cudaFree(p->h_rho);
     cudaFree(p->h_phi);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(p->h_rho2[b]);
+        cudaFree(p->h_phi2[b]);
+        p->h_rho2[b] = nullptr;
+        p->h_phi2[b] = nullptr;
+        if (p->ev_in[b]) cudaEventDestroy(p->ev_in[b]);
+        if (p->ev_solved[b]) cudaEventDestroy(p->ev_solved[b]);
+        if (p->ev_out[b]) cudaEventDestroy(p->ev_out[b]);
+        p->ev_in[b] = p->ev_solved[b] = p->ev_out[b] = nullptr;
+    }
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
+    p->s_in = p->s_out = nullptr;
     p->restr = p->work = p->lvl = p->crop = p->carry = p->vbuf = p->dbl_work = p->dbl_out = p->h_rho = nullptr;
     p->qdp_work = p->qdp_out = p->red = nullptr;
     p->h_phi = nullptr;
@@ -1059,6 +1076,55 @@ nm_status nm_potential_host(nm_plan_t p, const void* rho_host, double* phi_host,
     if (st != NM_OK) return st;
     NM_CUDA(cudaMemcpyAsync(phi_host, p->h_phi, cells * sizeof(double), cudaMemcpyDeviceToHost, s), "phi download");
     NM_CUDA(cudaStreamSynchronize(s), "nm_potential_host sync");
+    return NM_OK;
+}
+
+nm_status nm_potential_host_many(nm_plan_t p, int n, const void* const* rho_host, double* const* phi_host,
+                                 void* stream) {
+    if (!p || n < 0 || (n > 0 && (!rho_host || !phi_host))) return fail(NM_EINVAL, "nm_potential_host_many: bad arguments");
+    for (int i = 0; i < n; ++i)
+        if (!rho_host[i] || !phi_host[i]) return fail(NM_EINVAL, "nm_potential_host_many: null entry %d", i);
+    if (n == 0) return NM_OK;
+    const size_t cells = (size_t)p->L * p->N * p->N * p->N;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!p->h_rho2[0]) {
+        for (int b = 0; b < 2; ++b) {
+            NM_CUDA(cudaMalloc(&p->h_rho2[b], cells * p->es), "host-path staging");
+            NM_CUDA(cudaMalloc((void**)&p->h_phi2[b], cells * sizeof(double)), "host-path staging");
+            NM_CUDA(cudaEventCreateWithFlags(&p->ev_in[b], cudaEventDisableTiming), "event");
+            NM_CUDA(cudaEventCreateWithFlags(&p->ev_solved[b], cudaEventDisableTiming), "event");
+            NM_CUDA(cudaEventCreateWithFlags(&p->ev_out[b], cudaEventDisableTiming), "event");
+        }
+        NM_CUDA(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking), "copy stream");
+        NM_CUDA(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking), "copy stream");
+        p->ws_bytes += 2 * cells * (p->es + sizeof(double));
+    }
+    nm_status st = ensure_green(p, s);
+    if (st != NM_OK) return st;
+    // the copy streams start after whatever the caller queued on `stream`
+    NM_CUDA(cudaEventRecord(p->ev_solved[0], s), "event");
+    NM_CUDA(cudaStreamWaitEvent(p->s_in, p->ev_solved[0], 0), "event wait");
+    NM_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_solved[0], 0), "event wait");
+    for (int i = 0; i < n; ++i) {
+        const int b = i & 1;
+        if (i >= 2) {
+            // solve i-2 has read rho buffer b; its download has read phi buffer b
+            NM_CUDA(cudaStreamWaitEvent(p->s_in, p->ev_solved[b], 0), "event wait");
+            NM_CUDA(cudaStreamWaitEvent(s, p->ev_out[b], 0), "event wait");
+        }
+        NM_CUDA(cudaMemcpyAsync(p->h_rho2[b], rho_host[i], cells * p->es, cudaMemcpyHostToDevice, p->s_in),
+                "rho upload");
+        NM_CUDA(cudaEventRecord(p->ev_in[b], p->s_in), "event");
+        NM_CUDA(cudaStreamWaitEvent(s, p->ev_in[b], 0), "event wait");
+        if ((st = run_items({Item{p, p->h_rho2[b], p->h_phi2[b]}}, s)) != NM_OK) return st;
+        NM_CUDA(cudaEventRecord(p->ev_solved[b], s), "event");
+        NM_CUDA(cudaStreamWaitEvent(p->s_out, p->ev_solved[b], 0), "event wait");
+        NM_CUDA(cudaMemcpyAsync(phi_host[i], p->h_phi2[b], cells * sizeof(double), cudaMemcpyDeviceToHost, p->s_out),
+                "phi download");
+        NM_CUDA(cudaEventRecord(p->ev_out[b], p->s_out), "event");
+    }
+    NM_CUDA(cudaStreamSynchronize(p->s_out), "nm_potential_host_many sync");
+    NM_CUDA(cudaStreamSynchronize(s), "nm_potential_host_many sync");
     return NM_OK;
 }
 

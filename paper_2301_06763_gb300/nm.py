@@ -74,6 +74,7 @@ def lib():
             "nm_potential": (st, [P, P, P, P]),
             "nm_potential_host": (st, [P, P, P, P]),
             "nm_acceleration": (st, [P, P, P, P]),
+            "nm_potential_host_many": (st, [P, ctypes.c_int, P, P, P]),
             "nm_acceleration_ex": (st, [P, P, P, ctypes.c_int, ctypes.c_int, P]),
             "nm_workspace_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
             "nm_spectrum_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -248,6 +249,26 @@ class Plan:
         _check(lib().nm_potential_host(self.handle, ctypes.c_void_p(rho_np.ctypes.data),
                                        ctypes.c_void_p(phi_np.ctypes.data), _stream_handle(stream)))
         return phi
+
+    def potential_host_many(self, rhos, phis, stream=None):
+        """len(rhos) solves from host memory, uploads and downloads overlapped
+        with the solves (page-locked buffers: CPU tensors from pin_memory());
+        synchronous."""
+        want = np.float32 if self.precision == "fp32" else np.float64
+        n = len(rhos)
+        if len(phis) != n:
+            raise ValueError("rhos and phis differ in length")
+        rp, pp = (ctypes.c_void_p * max(n, 1))(), (ctypes.c_void_p * max(n, 1))()
+        for i, (r, f) in enumerate(zip(rhos, phis)):
+            rn = r.numpy() if hasattr(r, "numpy") and not isinstance(r, np.ndarray) else r
+            fn = f.numpy() if hasattr(f, "numpy") and not isinstance(f, np.ndarray) else f
+            if rn.dtype != want or rn.shape != self.shape or not rn.flags.c_contiguous:
+                raise ValueError("rho must be a C-contiguous %s array of shape %s" % (want, self.shape))
+            if fn.dtype != np.float64 or fn.shape != self.shape or not fn.flags.c_contiguous:
+                raise ValueError("phi must be a C-contiguous float64 array of shape %s" % (self.shape,))
+            rp[i], pp[i] = rn.ctypes.data, fn.ctypes.data
+        _check(lib().nm_potential_host_many(self.handle, n, rp, pp, _stream_handle(stream)))
+        return phis
 
     def schedule(self):
         sc = Schedule()

@@ -107,3 +107,21 @@ def test_autotune_picks_a_valid_schedule_and_caches_it(tmp_path, monkeypatch):
     with m.Plan(L, N, 1.0 / N, precision="fp32") as q:
         assert q.schedule() == sc
         assert rel_max(q.potential(rho).cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_pipelined_host_solves_equal_one_by_one(precision):
+    # nm_potential_host_many overlaps each solve's upload and download with the
+    # neighbouring solves on two staging sets; every result must equal the
+    # plain host-path solve of the same density
+    import torch
+    m = nm()
+    L, N = 3, 32
+    dt = np.float32 if precision == "fp32" else np.float64
+    rhos = [torch.from_numpy(wl.random_density(70 + i, L, N).astype(dt)).pin_memory() for i in range(5)]
+    phis = [torch.empty((L, N, N, N), dtype=torch.float64).pin_memory() for _ in range(5)]
+    with m.Plan(L, N, 1.0 / N, precision=precision) as p:
+        p.potential_host_many(rhos, phis)
+        for r, f in zip(rhos, phis):
+            ref = p.potential_host(r.numpy())
+            assert np.array_equal(f.numpy(), ref)
