@@ -48,7 +48,7 @@ class Request:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes, slots=4, precision="fp32", max_batch=64, device=None):
+    def __init__(self, hbm_budget_bytes, slots=4, precision="fp32", max_batch=64, device=None, interp="diagonal"):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -56,6 +56,7 @@ class Server:
         self.used = 0
         self.peak_used = 0
         self.precision = precision
+        self.interp = interp
         self.max_batch = int(max_batch)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         self.free = list(range(slots))
@@ -75,7 +76,7 @@ class Server:
         cells = r.levels * r.N ** 3
         b = cells * (_ES[self.precision] + 8)
         if with_plan:
-            b += nm.footprint_bytes(r.levels, r.N, r.dx0, r.G, self.precision, r.method)
+            b += nm.footprint_bytes(r.levels, r.N, r.dx0, r.G, self.precision, r.method, self.interp)
         return b
 
     def _take_plan(self, r):
@@ -154,7 +155,8 @@ class Server:
             self.queue.popleft()
             try:
                 if plan is None:
-                    plan = nm.Plan(r.levels, r.N, r.dx0, r.G, precision=self.precision, method=r.method)
+                    plan = nm.Plan(r.levels, r.N, r.dx0, r.G, precision=self.precision, method=r.method,
+                                   interp=self.interp)
                     need = self.request_bytes(r, with_plan=False) + plan.workspace_bytes()
             except Exception as e:          # invalid shape or allocation failure
                 r.error = str(e)
