@@ -513,6 +513,13 @@ def ours(args):
     dev_ms = max_over_ranks(torch, dist, dev_ms)
     dev64_ms, per64, _ = timed_loop(torch, p64, rho64, phis, args.steps, dist, stream)
     dev64_ms = max_over_ranks(torch, dist, dev64_ms)
+    # FP64-class accuracy from the FP32 pipe: double-float transforms
+    p64x = nm.Plan(L, N, w.dx0, precision="fp64x")
+    p64x.green()
+    for i in range(3):
+        p64x.potential(rho64[i % NSETS], phis[i % NSETS])
+    dev64x_ms, per64x, _ = timed_loop(torch, p64x, rho64, phis, args.steps, dist, stream)
+    dev64x_ms = max_over_ranks(torch, dist, dev64x_ms)
     clk = clocks.stop()
 
     # end to end through the host-buffer entry points (H2D + solve + D2H per
@@ -595,6 +602,9 @@ def ours(args):
         "fp64": {"value": world * args.steps / (dev64_ms / 1e3), "unit": "solves/s",
                  "ms_per_step": dev64_ms / args.steps, "p50_ms": pct(per64, 50),
                  "p99_ms": pct(per64, 99), "dtype": "f64"},
+        "fp64x": {"value": world * args.steps / (dev64x_ms / 1e3), "unit": "solves/s",
+                  "ms_per_step": dev64x_ms / args.steps, "p50_ms": pct(per64x, 50), "p99_ms": pct(per64x, 99),
+                  "dtype": "double-float (2 x f32)", "accuracy": "within 1e-12 of max|Phi| of the FP64 oracle"},
         "hbm": {"solve_algorithmic_bytes": solve_bytes,
                 "solve_gbs": solve_bytes / (ms_step * 1e-3) / 1e9,
                 "frac": solve_bytes / (ms_step * 1e-3) / 1e9 / peak},

@@ -78,7 +78,7 @@ typedef enum {
     NM_EUNSUPPORTED = 5   /* valid request this build does not implement       */
 } nm_status;
 
-enum { NM_FP64 = 0, NM_FP32 = 1 };
+enum { NM_FP64 = 0, NM_FP32 = 1, NM_FP64X = 2 };
 enum { NM_METHOD_ORIGINAL = 0, NM_METHOD_DIPOLE_PAIR = 1, NM_METHOD_DIPOLE_TRIPLE = 2, NM_METHOD_DIPOLE_TRIPLE_DIRECT = 3 };
 enum { NM_INTERP_TRILINEAR = 0, NM_INTERP_DIAGONAL = 1 };
 enum { NM_MAX_LEVELS = 16 };
@@ -88,7 +88,13 @@ typedef struct {
     int N;           /* cells per axis per level: a power of two, 4 .. 256      */
     double dx0;      /* coarsest cell size (> 0); level m has dx0 / 2^m         */
     double G;        /* gravitational constant (Eq. 9); nm_plan uses 1.0        */
-    int precision;   /* NM_FP64: all arithmetic in double.  NM_FP32: FFT passes,
+    int precision;   /* NM_FP64: all arithmetic in double.  NM_FP64X: densities
+                        and potentials in double, the transforms, spectrum
+                        multiply and cross-level sums in double-float (two
+                        floats, ~48 bits) on the FP32 pipe -- within 1e-12 of
+                        the double result, several times faster on parts whose
+                        FP64 rate is a small fraction of FP32 (original method,
+                        N >= 8; NM_EUNSUPPORTED otherwise).  NM_FP32: FFT passes,
                         spectrum multiply, interpolation and the sum of the
                         coarser levels' terms in float; Green spectrum built in
                         double; the final per-cell addition of that sum to the

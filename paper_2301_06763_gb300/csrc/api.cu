@@ -92,11 +92,13 @@ struct Spectrum {
     bool ready = false;
     double* d64 = nullptr;
     float* d32 = nullptr;
+    df* ddf = nullptr;
 };
 struct Twiddle {
     int dev = -1, P = 0;
     cpx<double>* d64 = nullptr;
     cpx<float>* d32 = nullptr;
+    cpx<df>* ddf = nullptr;
 };
 
 static std::mutex g_cache_mu;
@@ -111,22 +113,27 @@ static nm_status get_twiddle(int dev, int P, Twiddle** out) {
         if (t->dev == dev && t->P == P) { *out = t; return NM_OK; }
     std::vector<cpx<double>> h64(P);
     std::vector<cpx<float>> h32(P);
+    std::vector<cpx<df>> hdf(P);
     const double two_pi = 6.283185307179586476925286766559;
     for (int t = 0; t < P; ++t) {
         const double a = two_pi * (double)t / (double)P;
         h64[t] = {std::cos(a), -std::sin(a)};
         h32[t] = {(float)h64[t].re, (float)h64[t].im};
+        hdf[t] = {df(h64[t].re), df(h64[t].im)};
     }
     Twiddle* tw = new Twiddle();
     tw->dev = dev;
     tw->P = P;
     cudaError_t e = cudaMalloc(&tw->d64, sizeof(cpx<double>) * P);
     if (e == cudaSuccess) e = cudaMalloc(&tw->d32, sizeof(cpx<float>) * P);
+    if (e == cudaSuccess) e = cudaMalloc(&tw->ddf, sizeof(cpx<df>) * P);
+    if (e == cudaSuccess) e = cudaMemcpy(tw->ddf, hdf.data(), sizeof(cpx<df>) * P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(tw->d64, h64.data(), sizeof(cpx<double>) * P, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(tw->d32, h32.data(), sizeof(cpx<float>) * P, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(tw->d64);
         cudaFree(tw->d32);
+        cudaFree(tw->ddf);
         delete tw;
         return cuda_fail(e, "twiddle table");
     }
@@ -154,6 +161,7 @@ static void release_spectrum(Spectrum* s) {
     if (--s->refs > 0) return;
     cudaFree(s->d64);
     cudaFree(s->d32);
+    cudaFree(s->ddf);
     for (size_t i = 0; i < g_spectra.size(); ++i)
         if (g_spectra[i] == s) { g_spectra.erase(g_spectra.begin() + i); break; }
     delete s;
@@ -176,12 +184,14 @@ static nm_status build_spectrum(Spectrum* s, cudaStream_t stream) {
     cudaError_t e = cudaSuccess;
     if (!s->d64) e = cudaMalloc(&s->d64, n * sizeof(double));
     if (e == cudaSuccess && !s->d32) e = cudaMalloc(&s->d32, n * sizeof(float));
+    if (e == cudaSuccess && !s->ddf) e = cudaMalloc(&s->ddf, n * sizeof(df));
     if (e == cudaSuccess) e = cudaMalloc(&d_ctab, P * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&scratch, 2 * n * sizeof(double));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_ctab, ctab.data(), P * sizeof(double), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = run_green_octant(s->d64, scratch, d_ctab, N, self_term, stream);
     if (e == cudaSuccess) e = run_to_float(s->d64, s->d32, n, stream);
+    if (e == cudaSuccess) e = run_to_df(s->d64, s->ddf, n, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cudaFree(d_ctab);
     cudaFree(scratch);
@@ -263,6 +273,7 @@ struct nm_plan_s {
     int dev = 0;
     int N = 0, L = 0, P = 0;
     bool fp32 = false, dipole = false;
+    bool dfx = false;                 // NM_FP64X: transforms in double-float
     bool triple = false, triple_ds = false;   // three-level dipole scheme (Appendix B), Eq. B.6 variant
     size_t es = 8, cs = 16;           // bytes per real / complex value
     nm_schedule sched{1, 16, 0, 1, 1};   // level convolutions
@@ -388,7 +399,7 @@ std::string tune_key(nm_plan_t p) {
     for (auto& c : name)
         if (c == '"' || c == '|') c = '_';
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|N%d|L%d|%s|%s", name.c_str(), p->N, p->L, p->fp32 ? "fp32" : "fp64",
+    snprintf(buf, sizeof buf, "%s|N%d|L%d|%s|%s", name.c_str(), p->N, p->L, p->fp32 ? "fp32" : p->dfx ? "fp64x" : "fp64",
              p->triple ? (p->triple_ds ? "dipole3_ds" : "dipole3") : p->dipole ? "dipole" : "original");
     return buf;
 }
@@ -450,6 +461,7 @@ bool sched_valid(nm_plan_t p, const nm_schedule& sc) {
     if (sc.group < 1 || sc.group > p->npairs) return false;
     if (sc.radix != 8 && sc.radix != 16) return false;
     if (sc.radix == 16 && p->P < 16) return false;
+    if (p->dfx && sc.radix != 16) return false;
     if (sc.pipeline != 0 && sc.pipeline != 1) return false;
     if (sc.fuse != 0 && sc.fuse != 1) return false;
     if (sc.fuse && sc.radix != 16) return false;
@@ -507,7 +519,11 @@ static nm_status validate_options(const nm_options& o) {
         return fail(NM_EUNSUPPORTED, "N must be a power of two in [4, 256], got %d", o.N);
     if (!(o.dx0 > 0.0) || !std::isfinite(o.dx0)) return fail(NM_EINVAL, "dx0 must be finite and > 0");
     if (!std::isfinite(o.G)) return fail(NM_EINVAL, "G must be finite");
-    if (o.precision != NM_FP64 && o.precision != NM_FP32) return fail(NM_EINVAL, "bad precision %d", o.precision);
+    if (o.precision != NM_FP64 && o.precision != NM_FP32 && o.precision != NM_FP64X)
+        return fail(NM_EINVAL, "bad precision %d", o.precision);
+    if (o.precision == NM_FP64X && o.method != NM_METHOD_ORIGINAL)
+        return fail(NM_EUNSUPPORTED, "NM_FP64X is built for the original method only");
+    if (o.precision == NM_FP64X && o.N < 8) return fail(NM_EUNSUPPORTED, "NM_FP64X needs N >= 8");
     if (o.method != NM_METHOD_ORIGINAL && o.method != NM_METHOD_DIPOLE_PAIR && o.method != NM_METHOD_DIPOLE_TRIPLE &&
         o.method != NM_METHOD_DIPOLE_TRIPLE_DIRECT)
         return fail(NM_EINVAL, "bad method %d", o.method);
@@ -572,6 +588,7 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     p->L = o.levels;
     p->P = 2 * o.N;
     p->fp32 = o.precision == NM_FP32;
+    p->dfx = o.precision == NM_FP64X;
     p->dipole = o.method != NM_METHOD_ORIGINAL;
     p->triple = (o.method == NM_METHOD_DIPOLE_TRIPLE || o.method == NM_METHOD_DIPOLE_TRIPLE_DIRECT) && o.levels > 2;
     p->triple_ds = o.method == NM_METHOD_DIPOLE_TRIPLE_DIRECT;
@@ -766,26 +783,34 @@ void qdp_pairs(nm_plan_t p, const void* rho, std::vector<PairDesc<T>>& out) {
 template <typename T> const T* spec_of(const Spectrum* s);
 template <> const float* spec_of<float>(const Spectrum* s) { return s->d32; }
 template <> const double* spec_of<double>(const Spectrum* s) { return s->d64; }
+template <> const df* spec_of<df>(const Spectrum* s) { return s->ddf; }
 template <typename T> const cpx<T>* tw_of(const Twiddle* t);
 template <> const cpx<float>* tw_of<float>(const Twiddle* t) { return t->d32; }
 template <> const cpx<double>* tw_of<double>(const Twiddle* t) { return t->d64; }
+template <> const cpx<df>* tw_of<df>(const Twiddle* t) { return t->ddf; }
 
 template <typename T>
 cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, int geom, const nm_schedule& sc,
                      const T* spec, const cpx<T>* tw, cudaStream_t s) {
-    if (geom == 2) {
-        if constexpr (sizeof(T) == 4) return run_conv_qdp_f32(pairs, n, P, spec, tw, s);
-        else return run_conv_qdp_f64(pairs, n, P, spec, tw, s);
-    }
     const bool dbl = geom == 1;
-    const bool e16 = dbl || (sc.radix == 16 && P >= 16);
-    const int flags = (sc.tile ? CONV_WIDE : 0) | (sc.pipeline ? CONV_TMA : 0) | (sc.fuse ? CONV_FUSED : 0);
-    if constexpr (sizeof(T) == 4) {
-        return e16 ? run_conv_f32_e16(pairs, n, P, dbl, flags, spec, tw, s)
-                   : run_conv_f32_e8(pairs, n, P, dbl, flags, spec, tw, s);
+    if constexpr (is_df<T>::value) {
+        // level grids only (NM_FP64X is validated for the original method)
+        if (geom != 0) return cudaErrorInvalidValue;
+        return run_conv_dfx_e16(pairs, n, P, false, sc.tile ? CONV_WIDE : 0, spec, tw, s);
     } else {
-        return e16 ? run_conv_f64_e16(pairs, n, P, dbl, flags, spec, tw, s)
-                   : run_conv_f64_e8(pairs, n, P, dbl, flags, spec, tw, s);
+        if (geom == 2) {
+            if constexpr (sizeof(T) == 4) return run_conv_qdp_f32(pairs, n, P, spec, tw, s);
+            else return run_conv_qdp_f64(pairs, n, P, spec, tw, s);
+        }
+        const bool e16 = dbl || (sc.radix == 16 && P >= 16);
+        const int flags = (sc.tile ? CONV_WIDE : 0) | (sc.pipeline ? CONV_TMA : 0) | (sc.fuse ? CONV_FUSED : 0);
+        if constexpr (sizeof(T) == 4) {
+            return e16 ? run_conv_f32_e16(pairs, n, P, dbl, flags, spec, tw, s)
+                       : run_conv_f32_e8(pairs, n, P, dbl, flags, spec, tw, s);
+        } else {
+            return e16 ? run_conv_f64_e16(pairs, n, P, dbl, flags, spec, tw, s)
+                       : run_conv_f64_e8(pairs, n, P, dbl, flags, spec, tw, s);
+        }
     }
 }
 
@@ -794,9 +819,10 @@ nm_status enqueue_restrict(nm_plan_t p, const void* rho, cudaStream_t s) {
     const int L = p->L, N = p->N;
     const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
     for (int m = L - 2; m >= 0; --m) {
-        const T* child = (const T*)rho + (size_t)(m + 1) * N3;
-        const T* rchild = (m + 1 < L - 1) ? (const T*)p->restr + (size_t)(m + 1) * h3 : nullptr;
-        cudaError_t e = run_restrict<T>(child, rchild, (T*)p->restr + (size_t)m * h3, N, s);
+        using TIN = typename InOf<T>::type;
+        const TIN* child = (const TIN*)rho + (size_t)(m + 1) * N3;
+        const TIN* rchild = (m + 1 < L - 1) ? (const TIN*)p->restr + (size_t)(m + 1) * h3 : nullptr;
+        cudaError_t e = run_restrict<TIN>(child, rchild, (TIN*)p->restr + (size_t)m * h3, N, s);
         if (e != cudaSuccess) return cuda_fail(e, "restriction");
     }
     return NM_OK;
@@ -909,7 +935,7 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
     }
     // three-level scheme: level n+2's term on level n (n < L-2), reduced from
     // the quadrupled grid or summed directly (Eq. B.6)
-    for (const Item& it : items) {
+    if constexpr (!is_df<T>::value) for (const Item& it : items) {
         nm_plan_t p = it.p;
         if (!p->triple) continue;
         const int N = p->N;
@@ -940,10 +966,11 @@ nm_status ensure_green(nm_plan_t p, cudaStream_t s) {
 }
 
 nm_status enqueue_all(const std::vector<Item>& items, cudaStream_t s) {
-    std::vector<Item> f32, f64;
-    for (const Item& it : items) (it.p->fp32 ? f32 : f64).push_back(it);
+    std::vector<Item> f32, f64, fdf;
+    for (const Item& it : items) (it.p->fp32 ? f32 : it.p->dfx ? fdf : f64).push_back(it);
     nm_status st = NM_OK;
     if (!f64.empty()) st = enqueue_items<double>(f64, s);
+    if (st == NM_OK && !fdf.empty()) st = enqueue_items<df>(fdf, s);
     if (st == NM_OK && !f32.empty()) st = enqueue_items<float>(f32, s);
     return st;
 }

@@ -24,6 +24,7 @@
 //   4 yinv : slabs z < P/2: inverse along y, keep y < P/2
 //   5 xinv : rows (z, y) < P/2: inverse along x, keep x < P/2, scatter outputs
 #pragma once
+#include "dfloat.cuh"
 #include "fft.cuh"
 
 namespace nm {
@@ -75,11 +76,11 @@ __device__ __forceinline__ T src_value(const SrcField& f, T scale, int NL, int z
     if (cov) {
         if (f.mode == SRC_HOLE) return T(0);
         if (f.restr)
-            v = (T)((const TIN*)f.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)];
+            v = conv_in<T, TIN>(((const TIN*)f.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)]);
         else
-            v = (T)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
+            v = conv_in<T, TIN>(((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x]);
     } else {
-        v = (T)((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x];
+        v = conv_in<T, TIN>(((const TIN*)f.rho)[((size_t)z * NL + y) * NL + x]);
     }
     return v * scale;
 }
@@ -95,9 +96,9 @@ __device__ __forceinline__ cpx<T> src_pair(const SrcField& f0, const SrcField& f
                          (unsigned)(x - q) < (unsigned)h;
         T v;
         if (cov && f0.restr)
-            v = (T)((const TIN*)f0.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)];
+            v = conv_in<T, TIN>(((const TIN*)f0.restr)[((size_t)(z - q) * h + (y - q)) * h + (x - q)]);
         else
-            v = (T)((const TIN*)f0.rho)[((size_t)z * NL + y) * NL + x];
+            v = conv_in<T, TIN>(((const TIN*)f0.rho)[((size_t)z * NL + y) * NL + x]);
         return {v * s0, cov ? T(0) : v * s1};
     }
     return {src_value<T, TIN>(f0, s0, NL, z, y, x), src_value<T, TIN>(f1, s1, NL, z, y, x)};
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
             TIN tmp[VEC];
             *reinterpret_cast<int4*>(tmp) = __ldg(reinterpret_cast<const int4*>(base + i));
 #pragma unroll
-            for (int q = 0; q < VEC; ++q) stage[i + q] = (T)tmp[q];
+            for (int q = 0; q < VEC; ++q) stage[i + q] = conv_in<T, TIN>(tmp[q]);
         }
         __syncthreads();
         const int q = NIN / 4, h = NIN / 2;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
                 const bool cov = row_cov && (unsigned)(xi - q) < (unsigned)h;
                 T full = val;
                 if (cov && d.src[0].restr)
-                    full = (T)((const TIN*)d.src[0].restr)[((size_t)(zi - q) * h + (yi - q)) * h + (xi - q)];
+                    full = conv_in<T, TIN>(((const TIN*)d.src[0].restr)[((size_t)(zi - q) * h + (yi - q)) * h + (xi - q)]);
                 v[r].re = full * s0;
                 v[r].im = (hole && !cov) ? val * s1 : T(0);
             }
@@ -204,25 +205,25 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-template <typename T, int P, int E>
+template <typename T, typename TIN, int P, int E>
 __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvArgs<T> a, int npairs) {
     using G = Geo<P, E, 0>;
     constexpr int TPL = P / E, LINES = 256 / TPL, NIN = G::NIN;
     constexpr int TILE = LINES * NIN;                 // density values per tile
     constexpr int TILES = NIN * NIN / LINES;          // tiles per pair
-    constexpr int VEC = 16 / sizeof(T);
+    constexpr int VEC = 16 / sizeof(TIN);
     static_assert((NIN * NIN) % LINES == 0 && TILE % (256 * VEC) == 0, "tile shape");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
-    T* stage = reinterpret_cast<T*>(sm_lines + LINES * (P + P / E));   // [2][TILE]
+    TIN* stage = reinterpret_cast<TIN*>(sm_lines + LINES * (P + P / E));   // [2][TILE]
     load_twiddles(sm_tw, a.tw, P);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int total = npairs * TILES;
     auto issue = [&](int t, int b) {
         const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
-        const T* src = (const T*)a.pair[pr].src[0].rho + (size_t)row0 * NIN;
-        T* dst = stage + b * TILE;
+        const TIN* src = (const TIN*)a.pair[pr].src[0].rho + (size_t)row0 * NIN;
+        TIN* dst = stage + b * TILE;
 #pragma unroll
         for (int i = threadIdx.x * VEC; i < TILE; i += 256 * VEC) cp_async16(dst + i, src + i);
     };
@@ -242,17 +243,18 @@ __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvA
         const int q = NIN / 4, h = NIN / 2;
         const bool row_cov = (unsigned)(zi - q) < (unsigned)h && (unsigned)(yi - q) < (unsigned)h;
         const bool hole = d.src[1].mode == SRC_HOLE;
-        const T* st = stage + (k & 1) * TILE + line * NIN;
+        const TIN* st = stage + (k & 1) * TILE + line * NIN;
         cpx<T> v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             v[r] = {T(0), T(0)};
             if (G::live(r)) {
                 const int xi = j + r * (P / E);
-                const T val = st[xi];
+                const T val = conv_in<T, TIN>(st[xi]);
                 const bool cov = row_cov && (unsigned)(xi - q) < (unsigned)h;
                 T full = val;
-                if (cov && d.src[0].restr) full = ((const T*)d.src[0].restr)[((size_t)(zi - q) * h + (yi - q)) * h + (xi - q)];
+                if (cov && d.src[0].restr)
+                    full = conv_in<T, TIN>(((const TIN*)d.src[0].restr)[((size_t)(zi - q) * h + (yi - q)) * h + (xi - q)]);
                 v[r].re = full * s0;
                 v[r].im = (hole && !cov) ? val * s1 : T(0);
             }
@@ -298,10 +300,17 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
 }
 
 // ---------------------------------------------------------------- pass 3
-// At least 1024 resident threads per SM (4 CTAs of 256): the seam holds two
-// transforms' worth of live values, and more warps hide its load latency.
+// Resident threads per SM the z-seam's register cap aims at: 1024 (4 CTAs of
+// 256) for float and double -- the seam holds two transforms' worth of live
+// values, and more warps hide its load latency -- and 512 for double-float,
+// whose values take twice the registers.
+template <typename T, int NT> struct ZseamMinBlocks {
+    static constexpr int R = is_df<T>::value ? 512 : 1024;
+    static constexpr int value = R / NT > 0 ? R / NT : 1;
+};
+
 template <typename T, int P, int E, int TX, int GM>
-__global__ void __launch_bounds__(TX * P / E, (1024 / (TX * P / E)) > 0 ? 1024 / (TX * P / E) : 1)
+__global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::value))
     k_zseam(const __grid_constant__ ConvArgs<T> a) {
     using G = Geo<P, E, GM>;
     constexpr int H = P / 2 + 1;
@@ -333,7 +342,7 @@ __global__ void __launch_bounds__(TX * P / E, (1024 / (TX * P / E)) > 0 ? 1024 /
     for (int s = 0; s < E; ++s) {
         const int kz = out_index<P, E>(j, s);
         const int fz = kz <= P / 2 ? kz : P - kz;
-        const T g = __ldg(sp + (size_t)fz * H * H);
+        const T g = ldg_t<T>(sp + (size_t)fz * H * H);
         v[s].re *= g;
         v[s].im *= g;
     }

@@ -70,7 +70,7 @@ static cudaError_t fused_pass(const ConvArgs<T>& a, int np, bool fwd, cudaStream
 template <typename T, int P, int E, int W, int GM>
 static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStream_t s) {
     const bool tma = (flags & CONV_TMA) != 0;
-    if constexpr (GM == 0 && E == 16 && FusedShape<T, P>::OK) {
+    if constexpr (GM == 0 && E == 16 && !is_df<T>::value && FusedShape<T, P>::OK) {
         if (flags & CONV_FUSED) {
             constexpr int TX = Tile<P, E, W>::TX;
             const char* tag = sizeof(T) == 4 ? "f32" : "f64";
@@ -104,6 +104,7 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
         }
     }
     using Gm = Geo<P, E, GM>;
+    using TIN = typename InOf<T>::type;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     constexpr int TX = Tile<P, E, W>::TX;
@@ -114,7 +115,7 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
     // shared-memory limits are set once per kernel (thread-safe static init)
     static const cudaError_t prepared = [&]() {
         cudaError_t e;
-        if ((e = prep_kernel(k_xfwd<T, T, P, E, GM>, sm_x)) != cudaSuccess) return e;
+        if ((e = prep_kernel(k_xfwd<T, TIN, P, E, GM>, sm_x)) != cudaSuccess) return e;
         if ((e = prep_kernel(k_ypass<T, P, E, TX, false, GM>, sm_yz)) != cudaSuccess) return e;
         if ((e = prep_kernel(k_zseam<T, P, E, TX, GM>, sm_yz)) != cudaSuccess) return e;
         if ((e = prep_kernel(k_ypass<T, P, E, TX, true, GM>, sm_yz)) != cudaSuccess) return e;
@@ -137,26 +138,27 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
             for (int i = 0; i < np && pipe; ++i) {
                 const PairDesc<T>& d = a.pair[i];
                 pipe = d.src[0].mode == SRC_FULL && ((uintptr_t)d.src[0].rho & 15) == 0 &&
+                       (!d.src[0].restr || ((uintptr_t)d.src[0].restr & 7) == 0) &&
                        (d.src[1].mode == SRC_NONE || (d.src[1].mode == SRC_HOLE && d.src[1].rho == d.src[0].rho));
             }
             if (pipe) {
                 constexpr int TILE = LINES * Gm::NIN;
-                const size_t sm_p = sm_x + 2 * (size_t)TILE * sizeof(T);
+                const size_t sm_p = sm_x + 2 * (size_t)TILE * sizeof(TIN);
                 static int occ = -1;
                 static const cudaError_t prep_p = [&]() {
-                    cudaError_t e = prep_kernel(k_xfwd_pipe<T, P, E>, sm_p);
+                    cudaError_t e = prep_kernel(k_xfwd_pipe<T, TIN, P, E>, sm_p);
                     if (e == cudaSuccess)
-                        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_pipe<T, P, E>, 256, sm_p);
+                        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_pipe<T, TIN, P, E>, 256, sm_p);
                     return e;
                 }();
                 if (prep_p != cudaSuccess) return prep_p;
                 const int tiles = np * (rows_in / LINES);
                 int grid = (occ > 0 ? occ : 1) * sm_count();
                 if (grid > tiles) grid = tiles;
-                k_xfwd_pipe<T, P, E><<<grid, 256, sm_p, s>>>(a, np);
+                k_xfwd_pipe<T, TIN, P, E><<<grid, 256, sm_p, s>>>(a, np);
             }
         }
-        if (!pipe) k_xfwd<T, T, P, E, GM><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
+        if (!pipe) k_xfwd<T, TIN, P, E, GM><<<dim3((rows_in + LINES - 1) / LINES, np), 256, sm_x, s>>>(a);
     }
     {
         snprintf(nm_, sizeof nm_, "yfwd%s_%s_P%d", geo, tag, P);
@@ -167,7 +169,7 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
         snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
         bool done = false;
-        if constexpr (GM == 0) {
+        if constexpr (GM == 0 && !is_df<T>::value) {
             if (tma) {
                 cudaError_t e = zseam_tma<T, P, E, TX>(a, np, s);
                 if (e != cudaSuccess) return e;
@@ -209,7 +211,7 @@ template <typename T, int E>
 static cudaError_t conv_dispatch(const ConvArgs<T>& a, int np, int P, bool dbl, int flags,
                                  cudaStream_t s) {
     if (dbl) {
-        if constexpr (E == 16) {
+        if constexpr (E == 16 && !is_df<T>::value) {
             switch (P) {
                 case 16: return conv_passes<T, 16, 16, Widths<T>::NARROW, 1>(a, np, 0, s);
                 case 32: return conv_passes<T, 32, 16, Widths<T>::NARROW, 1>(a, np, 0, s);

@@ -36,6 +36,9 @@ cudaError_t run_conv_f64_e16(const PairDesc<double>* pairs, int npairs, int P, b
                              const double* spec, const cpx<double>* tw, cudaStream_t s);
 cudaError_t run_conv_f64_e8(const PairDesc<double>* pairs, int npairs, int P, bool dbl, int flags,
                             const double* spec, const cpx<double>* tw, cudaStream_t s);
+// Double-float passes (NM_FP64X), level grids, 16 values per thread.
+cudaError_t run_conv_dfx_e16(const PairDesc<df>* pairs, int npairs, int P, bool dbl, int flags, const df* spec,
+                             const cpx<df>* tw, cudaStream_t s);
 // Quadrupled-grid geometry (Appendix B), P = 8N, 16 values per thread.
 cudaError_t run_conv_qdp_f32(const PairDesc<float>* pairs, int npairs, int P, const float* spec,
                              const cpx<float>* tw, cudaStream_t s);
@@ -57,6 +60,7 @@ int sm_count();
 cudaError_t run_green_octant(double* out, double* scratch, const double* ctab, int N,
                              double self_term, cudaStream_t s);
 cudaError_t run_to_float(const double* in, float* out, size_t n, cudaStream_t s);
+cudaError_t run_to_df(const double* in, df* out, size_t n, cudaStream_t s);
 
 // Restriction of level m+1 onto level m's covered cells (mean of 2^3 children).
 template <typename TIN>

@@ -163,9 +163,11 @@ extern "C" nm_status nm_potential_noalloc(const nm_options* opt, const void* rho
     const nm_options o = *opt;
     if (o.levels < 1 || o.levels > NM_MAX_LEVELS || o.N < 4 || !pow2(o.N) || !(o.dx0 > 0.0) ||
         !std::isfinite(o.dx0) || !std::isfinite(o.G) ||
-        (o.precision != NM_FP64 && o.precision != NM_FP32) ||
+        (o.precision != NM_FP64 && o.precision != NM_FP32 && o.precision != NM_FP64X) ||
         (o.interp != NM_INTERP_TRILINEAR && o.interp != NM_INTERP_DIAGONAL))
         return record_error(NM_EINVAL, "nm_potential_noalloc: invalid options");
+    if (o.precision == NM_FP64X)
+        return record_error(NM_EUNSUPPORTED, "nm_potential_noalloc: NM_FP64X is not built here");
     if (o.method != NM_METHOD_ORIGINAL)
         return record_error(NM_EUNSUPPORTED, "nm_potential_noalloc: only the original method (Eq. 14)");
     const bool fp32 = o.precision == NM_FP32;

@@ -1,6 +1,7 @@
 // support.cu -- restriction, Green spectrum and final assembly kernels.
 #include "../../include/nm.h"
 #include "internal.h"
+#include "dfloat.cuh"
 
 namespace nm {
 
@@ -170,6 +171,18 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
         out[i] = (float)in[i];
 }
 
+__global__ void k_to_df(const double* __restrict__ in, df* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = df_from_double(in[i]);
+}
+
+cudaError_t run_to_df(const double* in, df* out, size_t n, cudaStream_t s) {
+    const int blocks = (int)((n + 255) / 256 < 152 * 32 ? (n + 255) / 256 : 152 * 32);
+    k_to_df<<<blocks, 256, 0, s>>>(in, out, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t run_to_float(const double* in, float* out, size_t n, cudaStream_t s) {
     const int blocks = (int)((n + 255) / 256 < 65536 ? (n + 255) / 256 : 65536);
     k_to_float<<<blocks, 256, 0, s>>>(in, out, n);
@@ -193,7 +206,8 @@ template <typename T>
 __device__ __forceinline__ void axis_stencil(int N, int lgr, int i, int& i0, T& t) {
     const int num = (N - 1) * ((1 << lgr) - 1) + 2 * i;
     i0 = num >> (lgr + 1);
-    t = (T)(num & ((2 << lgr) - 1)) * ((T)1 / (T)(2 << lgr));
+    // a dyadic fraction with at most 16 bits: exact in float
+    t = (T)((float)(num & ((2 << lgr) - 1)) * (1.0f / (float)(2 << lgr)));
 }
 
 // Exact float -> double in integer arithmetic (sign, exponent re-biased by
@@ -235,6 +249,20 @@ template <> struct Vec4<double> {
         v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
     }
 };
+template <> struct Vec4<df> {
+    static __device__ __forceinline__ void load(const df* p, df* v) {
+        const float4 q0 = reinterpret_cast<const float4*>(p)[0];
+        const float4 q1 = reinterpret_cast<const float4*>(p)[1];
+        v[0] = df(q0.x, q0.y); v[1] = df(q0.z, q0.w); v[2] = df(q1.x, q1.y); v[3] = df(q1.z, q1.w);
+    }
+};
+
+// A level's own potential b plus the cross-level sum acc, as the double that
+// phi stores: float and double widen each and add once in double; df sums in
+// df first, then one conversion.
+__device__ __forceinline__ double out_sum(float b, float acc) { return widen(b) + widen(acc); }
+__device__ __forceinline__ double out_sum(double b, double acc) { return b + acc; }
+__device__ __forceinline__ double out_sum(df b, df acc) { return df_to_double(b + acc); }
 
 // Eqs. 3-6 on one axis: level-(n-1) position of level-n index i (i >= -1) is
 // (N/2 + i)/2 - 1/4 = c + s/4: nearest coarse index c, diagonal step s.
@@ -280,6 +308,7 @@ cudaError_t run_carry(const CarryArgs<T>& a, cudaStream_t s) {
 }
 template cudaError_t run_carry<float>(const CarryArgs<float>&, cudaStream_t);
 template cudaError_t run_carry<double>(const CarryArgs<double>&, cudaStream_t);
+template cudaError_t run_carry<df>(const CarryArgs<df>&, cudaStream_t);
 
 // One thread per 4 consecutive cells along x (N >= 4): the z and y stencils of
 // each coarser level are shared by the 4 cells.
@@ -351,8 +380,8 @@ __global__ void k_assemble(const __grid_constant__ AssembleArgs<T> a, int lgN) {
             }
         }
         double2* out = reinterpret_cast<double2*>(a.phi + idx);
-        out[0] = make_double2(widen(b[0]) + widen(acc[0]), widen(b[1]) + widen(acc[1]));
-        out[1] = make_double2(widen(b[2]) + widen(acc[2]), widen(b[3]) + widen(acc[3]));
+        out[0] = make_double2(out_sum(b[0], acc[0]), out_sum(b[1], acc[1]));
+        out[1] = make_double2(out_sum(b[2], acc[2]), out_sum(b[3], acc[3]));
     }
 }
 
@@ -366,6 +395,7 @@ __device__ __forceinline__ float stencil_weight(int N, int lgr, int i, int& i0) 
 template <typename T> __device__ __forceinline__ T as_t(float f);
 template <> __device__ __forceinline__ float as_t<float>(float f) { return f; }
 template <> __device__ __forceinline__ double as_t<double>(float f) { return widen(f); }
+template <> __device__ __forceinline__ df as_t<df>(float f) { return df(f); }
 
 // Row-wise assembly (N >= 16): a team of N/4 threads owns one fine row
 // (level n, z, y), 4 cells per thread.  For each coarser level k the row's
@@ -449,8 +479,8 @@ __global__ void __launch_bounds__(256) k_assemble_rows(const __grid_constant__ A
             __syncthreads();
         }
         double2* out = reinterpret_cast<double2*>(a.phi + ((size_t)n << (3 * lgN)) + cell);
-        out[0] = make_double2(widen(b[0]) + widen(acc[0]), widen(b[1]) + widen(acc[1]));
-        out[1] = make_double2(widen(b[2]) + widen(acc[2]), widen(b[3]) + widen(acc[3]));
+        out[0] = make_double2(out_sum(b[0], acc[0]), out_sum(b[1], acc[1]));
+        out[1] = make_double2(out_sum(b[2], acc[2]), out_sum(b[3], acc[3]));
     }
 }
 
@@ -476,6 +506,7 @@ cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
 }
 template cudaError_t run_assemble<float>(const AssembleArgs<float>&, cudaStream_t);
 template cudaError_t run_assemble<double>(const AssembleArgs<double>&, cudaStream_t);
+template cudaError_t run_assemble<df>(const AssembleArgs<df>&, cudaStream_t);
 
 template <typename T>
 cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStream_t s) {
@@ -506,5 +537,6 @@ cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStr
 }
 template cudaError_t run_assemble_interp<float>(AssembleArgs<float>, int, float*, cudaStream_t);
 template cudaError_t run_assemble_interp<double>(AssembleArgs<double>, int, double*, cudaStream_t);
+template cudaError_t run_assemble_interp<df>(AssembleArgs<df>, int, df*, cudaStream_t);
 
 }  // namespace nm

@@ -17,10 +17,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnestconv.so")
 
 NM_OK, NM_EINVAL, NM_ENOMEM, NM_ECUDA, NM_ETIMEOUT, NM_EUNSUPPORTED = range(6)
-FP64, FP32 = 0, 1
+FP64, FP32, FP64X = 0, 1, 2
 ORIGINAL, DIPOLE_PAIR, DIPOLE_TRIPLE, DIPOLE_TRIPLE_DIRECT = 0, 1, 2, 3
 TRILINEAR, DIAGONAL = 0, 1
-_PREC = {"fp64": FP64, "fp32": FP32}
+_PREC = {"fp64": FP64, "fp32": FP32, "fp64x": FP64X}
 _METHOD = {"original": ORIGINAL, "dipole": DIPOLE_PAIR, "dipole3": DIPOLE_TRIPLE,
            "dipole3_ds": DIPOLE_TRIPLE_DIRECT}
 _INTERP = {"trilinear": TRILINEAR, "diagonal": DIAGONAL}

@@ -25,7 +25,7 @@ import numpy as np
 
 from . import nm
 
-_ES = {"fp32": 4, "fp64": 8}
+_ES = {"fp32": 4, "fp64": 8, "fp64x": 8}
 
 
 class Request:
