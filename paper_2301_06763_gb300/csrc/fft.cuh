@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace nm {
 
 template <typename T> struct alignas(2 * sizeof(T)) cpx { T re, im; };
@@ -46,6 +48,28 @@ __device__ __forceinline__ cpx<float> operator+(cpx<float> a, cpx<float> b) {
 __device__ __forceinline__ cpx<float> operator-(cpx<float> a, cpx<float> b) {
     const float2 r = __fadd2_rn(make_float2(a.re, a.im), make_float2(-b.re, -b.im));
     return {r.x, r.y};
+}
+// The same pairing for double-float complex values: the real and imaginary
+// parts go through the identical sequence of the double-float sum, so each of
+// its steps is one FADD2 on (re, im) pairs of high and of low words.
+__device__ __forceinline__ cpx<df> df_cadd(float2 ah, float2 al, float2 bh, float2 bl) {
+    const float2 s = __fadd2_rn(ah, bh);
+    const float2 bb = __fadd2_rn(s, make_float2(-ah.x, -ah.y));
+    const float2 t = __fadd2_rn(s, make_float2(-bb.x, -bb.y));
+    float2 e = __fadd2_rn(__fadd2_rn(ah, make_float2(-t.x, -t.y)), __fadd2_rn(bh, make_float2(-bb.x, -bb.y)));
+    e = __fadd2_rn(e, __fadd2_rn(al, bl));
+    const float2 r = __fadd2_rn(s, e);
+    const float2 u = __fadd2_rn(r, make_float2(-s.x, -s.y));
+    const float2 lo = __fadd2_rn(e, make_float2(-u.x, -u.y));
+    return {df(r.x, lo.x), df(r.y, lo.y)};
+}
+__device__ __forceinline__ cpx<df> operator+(cpx<df> a, cpx<df> b) {
+    return df_cadd(make_float2(a.re.hi, a.im.hi), make_float2(a.re.lo, a.im.lo), make_float2(b.re.hi, b.im.hi),
+                   make_float2(b.re.lo, b.im.lo));
+}
+__device__ __forceinline__ cpx<df> operator-(cpx<df> a, cpx<df> b) {
+    return df_cadd(make_float2(a.re.hi, a.im.hi), make_float2(a.re.lo, a.im.lo), make_float2(-b.re.hi, -b.im.hi),
+                   make_float2(-b.re.lo, -b.im.lo));
 }
 #endif
 
@@ -108,6 +132,64 @@ template <typename T, bool INV> __device__ __forceinline__ cpx<T> rotc(cpx<T> a,
     if (INV) return {a.re * c - a.im * s, a.re * s + a.im * c};
     return {a.re * c + a.im * s, a.im * c - a.re * s};
 }
+
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+// Double-float complex products, paired as above: two double-float products
+// per instruction sequence (FMUL2 / FFMA2 on pairs of high and low words).
+struct df2 { float2 h, l; };
+__device__ __forceinline__ df2 df2_of(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ df2 df2_mul(df2 x, df2 y) {
+    const float2 p = __fmul2_rn(x.h, y.h);
+    float2 e = __ffma2_rn(x.h, y.h, neg2(p));
+    e = __ffma2_rn(x.h, y.l, e);
+    e = __ffma2_rn(x.l, y.h, e);
+    const float2 r = __fadd2_rn(p, e);
+    return {r, __fadd2_rn(e, neg2(__fadd2_rn(r, neg2(p))))};
+}
+__device__ __forceinline__ cpx<df> df2_sum(df2 x, df2 y) { return df_cadd(x.h, x.l, y.h, y.l); }
+__device__ __forceinline__ df2 df2_of(cpx<df> c) { return df2_of(c.re, c.im); }
+__device__ __forceinline__ df2 df2_add(df2 x, df2 y) { return df2_of(df_cadd(x.h, x.l, y.h, y.l)); }
+
+__device__ __forceinline__ cpx<df> cmul(cpx<df> a, cpx<df> b) {
+    // (ar, ar) (br, bi) + (ai, ai) (-bi, br)
+    return df2_sum(df2_mul(df2_of(a.re, a.re), df2_of(b.re, b.im)), df2_mul(df2_of(a.im, a.im), df2_of(-b.im, b.re)));
+}
+__device__ __forceinline__ cpx<df> cmulc(cpx<df> a, cpx<df> b) {
+    // (ar, ar) (br, -bi) + (ai, ai) (bi, br)
+    return df2_sum(df2_mul(df2_of(a.re, a.re), df2_of(b.re, -b.im)), df2_mul(df2_of(a.im, a.im), df2_of(b.im, b.re)));
+}
+template <> __device__ __forceinline__ cpx<df> rotc<df, false>(cpx<df> a, df c, df s) {
+    return df2_sum(df2_mul(df2_of(a.re, a.im), df2_of(c, c)), df2_mul(df2_of(a.im, a.re), df2_of(s, -s)));
+}
+template <> __device__ __forceinline__ cpx<df> rotc<df, true>(cpx<df> a, df c, df s) {
+    return df2_sum(df2_mul(df2_of(a.re, a.im), df2_of(c, c)), df2_mul(df2_of(a.im, a.re), df2_of(-s, s)));
+}
+template <> __device__ __forceinline__ cpx<df> rot8<df, false>(cpx<df> a) {
+    const df h = df(0.70710678118654752440);
+    const cpx<df> t = df2_sum(df2_of(a.re, a.im), df2_of(a.im, -a.re));
+    const df2 r = df2_mul(df2_of(t), df2_of(h, h));
+    return {df(r.h.x, r.l.x), df(r.h.y, r.l.y)};
+}
+template <> __device__ __forceinline__ cpx<df> rot8<df, true>(cpx<df> a) {
+    const df h = df(0.70710678118654752440);
+    const cpx<df> t = df2_sum(df2_of(a.re, a.re), df2_of(-a.im, a.im));
+    const df2 r = df2_mul(df2_of(t), df2_of(h, h));
+    return {df(r.h.x, r.l.x), df(r.h.y, r.l.y)};
+}
+template <> __device__ __forceinline__ cpx<df> rot8_3<df, false>(cpx<df> a) {
+    const df h = df(0.70710678118654752440);
+    const cpx<df> t = df2_sum(df2_of(-a.re, -a.re), df2_of(a.im, -a.im));
+    const df2 r = df2_mul(df2_of(t), df2_of(h, h));
+    return {df(r.h.x, r.l.x), df(r.h.y, r.l.y)};
+}
+template <> __device__ __forceinline__ cpx<df> rot8_3<df, true>(cpx<df> a) {
+    const df h = df(0.70710678118654752440);
+    const cpx<df> t = df2_sum(df2_of(-a.re, a.re), df2_of(-a.im, -a.im));
+    const df2 r = df2_mul(df2_of(t), df2_of(h, h));
+    return {df(r.h.x, r.l.x), df(r.h.y, r.l.y)};
+}
+#endif
 
 // 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.  DFT4 over n1 for each
 // n2, multiply by W16^(n2 k1), DFT4 over n2 for each k1.
