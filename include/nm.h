@@ -268,6 +268,20 @@ nm_status nm_device_status(int clear);
  * invalid.  Process-wide. */
 nm_status nm_debug_fault_timeout(int on);
 
+/* Test hook, host-side fault injection: with n > 0 the n-th workspace
+ * allocation made by the next plan creations fails as if the device were out
+ * of memory (nm_plan_ex then returns NM_ENOMEM after freeing what it had
+ * allocated); 0 disarms.  NM_EINVAL for n < 0. */
+nm_status nm_debug_fail_alloc(int n);
+
+/* Test hook: transform `lines` contiguous lines of P complex values (P a
+ * power of two, 8..1024) in place with the passes' line transform (fft.cuh):
+ * forward X[k] = sum_j x[j] exp(-2 pi i jk/P), or with `inverse` the + sign and
+ * no 1/P.  `data` is device memory, interleaved re/im, double for NM_FP64 and
+ * float for NM_FP32; asynchronous on `stream`.  NM_EINVAL for bad arguments,
+ * NM_EUNSUPPORTED for P out of range. */
+nm_status nm_debug_fft(int P, int precision, int inverse, int lines, void* data, void* stream);
+
 /* Number of kernels this library has launched in the process so far. */
 uint64_t nm_kernel_launches(void);
 

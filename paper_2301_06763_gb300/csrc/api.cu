@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nm.h"
 #include "internal.h"
 
@@ -31,6 +33,7 @@ static std::mutex g_prof_mu;
 static std::vector<ProfRecord> g_prof;
 
 ProfScope::ProfScope(const char* name, int units, cudaStream_t stream) : s(stream) {
+    nvtxRangePushA(name);   // host-side range per pass launch, for timeline tools
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
     ProfRecord r{name, units, nullptr, nullptr};
     if (cudaEventCreate(&r.a) != cudaSuccess) return;
@@ -41,6 +44,7 @@ ProfScope::ProfScope(const char* name, int units, cudaStream_t stream) : s(strea
     g_prof.push_back(r);
 }
 ProfScope::~ProfScope() {
+    nvtxRangePop();
     if (idx < 0) return;
     cudaEvent_t b;
     {
@@ -205,6 +209,7 @@ static std::mutex g_dev_mu;
 static int* g_status[64] = {};
 static int g_sms[64] = {};
 static std::atomic<int> g_fault_timeout{0};
+static std::atomic<int> g_fail_alloc{0};   // > 0: the n-th next plan workspace allocation fails
 
 int* device_status_word() {
     int dev = 0;
@@ -615,6 +620,11 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** ptr, size_t bytes) {
         if (e != cudaSuccess || bytes == 0) return;
+        // test hook: the armed allocation fails as if the device were full
+        if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+            e = cudaErrorMemoryAllocation;
+            return;
+        }
         e = cudaMalloc(ptr, bytes);
         if (e == cudaSuccess) p->ws_bytes += bytes;
     };
@@ -1313,6 +1323,12 @@ nm_status nm_device_status(int clear) {
     NM_CUDA(cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost), "nm_device_status read");
     if (clear) NM_CUDA(cudaMemset(w, 0, sizeof(int)), "nm_device_status clear");
     if (v == NM_ETIMEOUT) return fail(NM_ETIMEOUT, "a bounded device-side wait ran out");
+    return NM_OK;
+}
+
+nm_status nm_debug_fail_alloc(int n) {
+    if (n < 0) return fail(NM_EINVAL, "nm_debug_fail_alloc: n must be >= 0");
+    g_fail_alloc.store(n);
     return NM_OK;
 }
 

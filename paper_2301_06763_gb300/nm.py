@@ -74,6 +74,8 @@ def lib():
             "nm_potential": (st, [P, P, P, P]),
             "nm_potential_host": (st, [P, P, P, P]),
             "nm_acceleration": (st, [P, P, P, P]),
+            "nm_debug_fail_alloc": (st, [ctypes.c_int]),
+            "nm_debug_fft": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]),
             "nm_potential_host_many": (st, [P, ctypes.c_int, P, P, P]),
             "nm_acceleration_ex": (st, [P, P, P, ctypes.c_int, ctypes.c_int, P]),
             "nm_workspace_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -149,6 +151,25 @@ def device_status(clear=True):
 def debug_fault_timeout(on):
     """Test hook: make the TMA-fed kernels' waits run out (see nm.h)."""
     _check(lib().nm_debug_fault_timeout(1 if on else 0))
+
+
+def debug_fail_alloc(n):
+    """Test hook: the n-th next plan workspace allocation fails (see nm.h)."""
+    _check(lib().nm_debug_fail_alloc(int(n)))
+
+
+def debug_fft(data, inverse=False, stream=None):
+    """Test hook: transform the rows of ``data`` (a contiguous CUDA complex64 or
+    complex128 tensor of shape (lines, P)) in place with the passes' line
+    transform."""
+    import torch
+    if not data.is_cuda or not data.is_contiguous() or data.dim() != 2 or \
+            data.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError("data must be a contiguous CUDA complex tensor of shape (lines, P)")
+    prec = FP32 if data.dtype == torch.complex64 else FP64
+    _check(lib().nm_debug_fft(int(data.shape[1]), prec, 1 if inverse else 0, int(data.shape[0]),
+                              ctypes.c_void_p(data.data_ptr()), _stream_handle(stream)))
+    return data
 
 
 def profile_enable(on=True):
