@@ -467,7 +467,9 @@ bool sched_valid(nm_plan_t p, const nm_schedule& sc) {
     if (sc.radix != 8 && sc.radix != 16) return false;
     if (sc.radix == 16 && p->P < 16) return false;
     if (p->dfx && sc.radix != 16) return false;
-    if (sc.pipeline != 0 && sc.pipeline != 1) return false;
+    if (sc.pipeline < 0 || sc.pipeline > 2) return false;
+    // two columns per thread: FP32 level grids, 16 values per thread, P >= 64
+    if (sc.pipeline == 2 && (!p->fp32 || p->dfx || sc.radix != 16 || p->P < 64 || sc.fuse)) return false;
     if (sc.fuse != 0 && sc.fuse != 1) return false;
     if (sc.fuse && sc.radix != 16) return false;
     return sc.tile == 0 || sc.tile == 1;
@@ -607,7 +609,10 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     p->sched.group = default_group(work_buf_bytes(p), p->npairs);
     p->sched.radix = p->P >= 16 ? 16 : 8;
     p->sched.tile = 0;
-    p->sched.pipeline = 0;
+    // FP32 at P >= 256: the z-seam with two columns per thread (measured
+    // faster on the 6 x 128^3 mesh); smaller FFT sizes keep one column per
+    // thread unless the autotuner finds otherwise
+    p->sched.pipeline = (p->fp32 && !p->dfx && p->P >= 256) ? 2 : 0;
     p->sched.fuse = 0;
     nm_schedule tuned;
     if (tune_lookup(p, &tuned) && sched_valid(p, tuned)) p->sched = tuned;
@@ -813,7 +818,8 @@ cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, int geom, const nm_
             else return run_conv_qdp_f64(pairs, n, P, spec, tw, s);
         }
         const bool e16 = dbl || (sc.radix == 16 && P >= 16);
-        const int flags = (sc.tile ? CONV_WIDE : 0) | (sc.pipeline ? CONV_TMA : 0) | (sc.fuse ? CONV_FUSED : 0);
+        const int flags = (sc.tile ? CONV_WIDE : 0) | (sc.pipeline == 1 ? CONV_TMA : 0) |
+                          (sc.pipeline == 2 ? CONV_PAIRED : 0) | (sc.fuse ? CONV_FUSED : 0);
         if constexpr (sizeof(T) == 4) {
             return e16 ? run_conv_f32_e16(pairs, n, P, dbl, flags, spec, tw, s)
                        : run_conv_f32_e8(pairs, n, P, dbl, flags, spec, tw, s);
@@ -1021,8 +1027,8 @@ nm_status run_items(const std::vector<Item>& items, cudaStream_t s) {
         key.push_back(it.rho);
         key.push_back(it.phi);
         const nm_schedule& sc = it.p->sched;
-        key.push_back((const void*)(uintptr_t)((sc.group << 12) | (sc.radix << 3) | (sc.fuse << 2) |
-                                               (sc.tile << 1) | sc.pipeline));
+        key.push_back((const void*)(uintptr_t)((sc.group << 12) | (sc.radix << 4) | (sc.fuse << 3) |
+                                               (sc.tile << 2) | sc.pipeline));
     }
     for (const Item& it : items) {
         nm_status st = ensure_green(it.p, s);
@@ -1193,7 +1199,8 @@ nm_status nm_set_schedule(nm_plan_t p, const nm_schedule* sc) {
     if (!p || !sc) return fail(NM_EINVAL, "nm_set_schedule: null argument");
     if (!sched_valid(p, *sc))
         return fail(NM_EINVAL,
-                    "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile and pipeline 0 or 1",
+                    "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile 0 or 1, pipeline 0, 1 "
+                    "or 2 (2: FP32, radix 16, P >= 64, not fused)",
                     p->npairs);
     nm_status st = ensure_work_slots(p, sc->group);
     if (st != NM_OK) return st;
@@ -1212,7 +1219,7 @@ nm_status nm_autotune(nm_plan_t p, const void* rho, double* phi, int reps, void*
     for (int g : groups)
         for (int radix : {16, 8})
             for (int tile : {0, 1})
-                for (int pipe : {1, 0})
+                for (int pipe : {2, 1, 0})
                     for (int fuse : {1, 0}) {
                         nm_schedule c{g, radix, tile, pipe, fuse};
                         if (!sched_valid(p, c)) continue;

@@ -110,9 +110,17 @@ template <int P, int E, int GM> struct Geo {
     static constexpr int OFF = GM == 0 ? 0 : GM == 1 ? P / 8 : 3 * P / 16;        // its offset in the domain
     static constexpr int NOUT = P / 2;                                            // output window
     // first-pass register r holds x[j + r P/E]: nonzero only for these r
-    __device__ static constexpr bool live(int r) {
+    __host__ __device__ static constexpr bool live(int r) {
         return GM == 0 ? (r < E / 2) : GM == 1 ? (r >= E / 8 && r < 3 * E / 8) : (r >= 3 * E / 16 && r < 5 * E / 16);
     }
+    // the same as a register mask, for the first pass of a forward transform
+    __host__ __device__ static constexpr unsigned live_mask() {
+        unsigned m = 0;
+        for (int r = 0; r < E; ++r)
+            if (live(r)) m |= 1u << r;
+        return m;
+    }
+    static constexpr unsigned LIVE = live_mask();
 };
 
 // ---------------------------------------------------------------- pass 1
@@ -180,8 +188,8 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
         }
     }
     __syncthreads();
-    fft_line<T, P, E, false>(v, j, sm_tw,
-                             LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
+    fft_line<T, P, E, false, G::LIVE, false>(v, j, sm_tw,
+                                             LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
     if (valid) {
         cpx<T>* dst = d.work + ((size_t)(zi + G::OFF) * P + (yi + G::OFF)) * P;
 #pragma unroll
@@ -259,8 +267,8 @@ __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvA
                 v[r].im = (hole && !cov) ? val * s1 : T(0);
             }
         }
-        fft_line<T, P, E, false>(v, j, sm_tw,
-                                 LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
+        fft_line<T, P, E, false, G::LIVE, false>(v, j, sm_tw,
+                                                 LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
         cpx<T>* out = d.work + ((size_t)zi * P + yi) * P;
 #pragma unroll
         for (int s = 0; s < E; ++s) out[out_index<P, E>(j, s)] = v[s];
@@ -291,7 +299,7 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
         else v[r] = {T(0), T(0)};
     }
     __syncthreads();
-    fft_line<T, P, E, INV>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
+    fft_line<T, P, E, INV, INV ? 0xFFFFu : G::LIVE, false>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const int e = out_index<P, E>(j, s);
@@ -334,7 +342,7 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
     }
     __syncthreads();
     const LineView<T, TX, false> view{sm_tile + l};
-    fft_line<T, P, E, false>(v, j, sm_tw, view);
+    fft_line<T, P, E, false, G::LIVE>(v, j, sm_tw, view);
     const int fy = y <= P / 2 ? y : P - y;
     const int fx = x <= P / 2 ? x : P - x;
     const T* sp = a.spec + (size_t)fy * H + fx;
@@ -347,11 +355,79 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
         v[s].im *= g;
     }
     seam_permute<T, P, E>(v);
-    fft_line<T, P, E, true>(v, j, sm_tw, view);
+    fft_line<T, P, E, true, 0xFFFFu, false>(v, j, sm_tw, view);
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const int e = out_index<P, E>(j, s);
         if (e < G::NOUT) col[(size_t)e * P * P] = v[s];
+    }
+}
+
+// Pass 3 in FP32 with two neighbouring columns per thread.  The lines (ky, x)
+// and (ky, x + 1) go through identical arithmetic, so the thread carries them
+// as one transform over cpx<f2> (lane 0 = column x, lane 1 = column x + 1):
+// the twiddle and spectrum products then take half the instructions of two
+// separate float transforms, and each shared-memory access moves both lines.
+// TX columns per CTA, TX / 2 threads across them; the spectrum row of the two
+// columns is read per lane (the fold P - x runs backwards).
+// Register budget: 512 resident threads per SM (128 registers each), the
+// same 1024 lines in flight per SM as the one-column kernel.
+template <int NT> struct Zseam2MinBlocks {
+    static constexpr int value = 512 / NT > 0 ? 512 / NT : 1;
+};
+
+template <int P, int E, int TX, int GM>
+__global__ void __launch_bounds__(TX / 2 * P / E, Zseam2MinBlocks<TX / 2 * P / E>::value)
+    k_zseam2(const __grid_constant__ ConvArgs<float> a) {
+    using G = Geo<P, E, GM>;
+    constexpr int H = P / 2 + 1, TX2 = TX / 2;
+    static_assert(TX % 2 == 0, "column pairs");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<f2>* sm_tw = reinterpret_cast<cpx<f2>*>(smem_raw);
+    cpx<f2>* sm_tile = sm_tw + P;
+    const PairDesc<float>& d = a.pair[blockIdx.z];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const cpx<float> w = a.tw[i];
+        sm_tw[i] = {f2(w.re, w.re), f2(w.im, w.im)};
+    }
+    const int l = threadIdx.x % TX2, j = threadIdx.x / TX2;
+    __builtin_assume(j < P / E);
+    const int y = blockIdx.y;
+    const int x = blockIdx.x * TX + 2 * l;
+    cpx<float>* col = d.work + (size_t)y * P + x;      // columns x, x + 1: element z at col[z * P * P]
+    cpx<f2> v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        if (G::live(r)) {
+            const float4 q = *reinterpret_cast<const float4*>(col + (size_t)(j + r * (P / E)) * P * P);
+            v[r] = {f2(q.x, q.z), f2(q.y, q.w)};
+        } else {
+            v[r] = {f2(0), f2(0)};
+        }
+    }
+    __syncthreads();
+    const LineView<f2, TX2, false> view{sm_tile + l};
+    fft_line<f2, P, E, false, G::LIVE>(v, j, sm_tw, view);
+    const int fy = y <= P / 2 ? y : P - y;
+    const int fx0 = x <= P / 2 ? x : P - x;
+    const int fx1 = x + 1 <= P / 2 ? x + 1 : P - x - 1;
+    const float* sp = a.spec + (size_t)fy * H;
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const int kz = out_index<P, E>(j, s);
+        const int fz = kz <= P / 2 ? kz : P - kz;
+        const float* row = sp + (size_t)fz * H * H;
+        const f2 g(__ldg(row + fx0), __ldg(row + fx1));
+        v[s].re *= g;
+        v[s].im *= g;
+    }
+    seam_permute<f2, P, E>(v);
+    fft_line<f2, P, E, true, 0xFFFFu, false>(v, j, sm_tw, view);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const int e = out_index<P, E>(j, s);
+        if (e < G::NOUT)
+            *reinterpret_cast<float4*>(col + (size_t)e * P * P) = make_float4(v[s].re.x, v[s].im.x, v[s].re.y, v[s].im.y);
     }
 }
 
@@ -388,8 +464,8 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = valid ? src[j + r * (P / E)] : cpx<T>{T(0), T(0)};
     __syncthreads();
-    fft_line<T, P, E, true>(v, j, sm_tw,
-                            LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
+    fft_line<T, P, E, true, 0xFFFFu, false>(v, j, sm_tw,
+                                            LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
     if (valid) {
 #pragma unroll
         for (int s = 0; s < E; ++s) {

@@ -1,0 +1,35 @@
+// conv_f32_pair.cu -- the FP32 z-seam with two columns per thread (k_zseam2),
+// level grids, 16 values per thread, for both column-tile widths.
+#include "internal.h"
+
+namespace nm {
+
+template <int P, int TX>
+static cudaError_t launch_zseam2(const ConvArgs<float>& a, int np, cudaStream_t s) {
+    constexpr int E = 16, NT = TX / 2 * P / E;
+    const size_t smem = (size_t)P * sizeof(cpx<f2>) + (size_t)(TX / 2) * P * sizeof(cpx<f2>);
+    static const cudaError_t prep =
+        cudaFuncSetAttribute(k_zseam2<P, E, TX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (prep != cudaSuccess) return prep;
+    k_zseam2<P, E, TX, 0><<<dim3(P / TX, P, np), NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TX>
+static cudaError_t zseam2_p(const ConvArgs<float>& a, int np, int P, cudaStream_t s) {
+    switch (P) {
+        case 64: return launch_zseam2<64, TX>(a, np, s);
+        case 128: return launch_zseam2<128, TX>(a, np, s);
+        case 256: return launch_zseam2<256, TX>(a, np, s);
+        case 512: return launch_zseam2<512, TX>(a, np, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t run_zseam_paired_f32(const ConvArgs<float>& a, int np, int P, int TX, cudaStream_t s) {
+    if (TX == 16) return zseam2_p<16>(a, np, P, s);
+    if (TX == 32) return zseam2_p<32>(a, np, P, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace nm

@@ -169,8 +169,15 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
         snprintf(nm_, sizeof nm_, "zseam%s_%s_P%d", geo, tag, P);
         ProfScope ps(nm_, np, s);
         bool done = false;
+        if constexpr (GM == 0 && E == 16 && P >= 64 && sizeof(T) == 4 && !is_df<T>::value) {
+            if (flags & CONV_PAIRED) {
+                cudaError_t e = run_zseam_paired_f32(a, np, P, TX, s);
+                if (e != cudaSuccess) return e;
+                done = true;
+            }
+        }
         if constexpr (GM == 0 && !is_df<T>::value) {
-            if (tma) {
+            if (!done && tma) {
                 cudaError_t e = zseam_tma<T, P, E, TX>(a, np, s);
                 if (e != cudaSuccess) return e;
                 done = true;

@@ -73,8 +73,42 @@ __device__ __forceinline__ cpx<df> operator-(cpx<df> a, cpx<df> b) {
 }
 #endif
 
+// Two float lanes operated on together: the real parts of two complex values
+// of two different lines form one f2, their imaginary parts another, so a
+// complex value of type cpx<f2> carries the same element of two lines and
+// every step of the transform (sums, twiddle products, scaling) acts on both
+// lines with one paired instruction.  With the twiddles broadcast to both
+// lanes, a complex product costs 2 paired multiply-adds per line pair where
+// cpx<float> needs 4 scalar ones per line.
+struct alignas(8) f2 {
+    float x, y;
+    f2() = default;
+    __host__ __device__ constexpr f2(float a, float b) : x(a), y(b) {}
+    __host__ __device__ explicit constexpr f2(double a) : x((float)a), y((float)a) {}
+    __host__ __device__ explicit constexpr f2(int a) : x((float)a), y((float)a) {}
+};
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+__device__ __forceinline__ float2 as_f2(f2 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ f2 of_f2(float2 a) { return {a.x, a.y}; }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return of_f2(__fadd2_rn(as_f2(a), as_f2(b))); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return of_f2(__fadd2_rn(as_f2(a), make_float2(-b.x, -b.y))); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return of_f2(__fmul2_rn(as_f2(a), as_f2(b))); }
+// a * b + c, one rounding per lane
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return of_f2(__ffma2_rn(as_f2(a), as_f2(b), as_f2(c))); }
+#else
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return {a.x * b.x, a.y * b.y}; }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return {fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)}; }
+#endif
+__device__ __forceinline__ f2 operator-(f2 a) { return {-a.x, -a.y}; }
+__device__ __forceinline__ f2& operator*=(f2& a, f2 b) { return a = a * b; }
+
 template <typename T> __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
     return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ cpx<f2> cmul(cpx<f2> a, cpx<f2> b) {
+    return {fma2(-a.im, b.im, a.re * b.re), fma2(a.re, b.im, a.im * b.re)};
 }
 // a * conj(b)
 template <typename T> __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
@@ -131,6 +165,15 @@ template <typename T, bool INV> __device__ __forceinline__ void dft8(cpx<T>* v) 
 template <typename T, bool INV> __device__ __forceinline__ cpx<T> rotc(cpx<T> a, T c, T s) {
     if (INV) return {a.re * c - a.im * s, a.re * s + a.im * c};
     return {a.re * c + a.im * s, a.im * c - a.re * s};
+}
+template <> __device__ __forceinline__ cpx<f2> rotc<f2, false>(cpx<f2> a, f2 c, f2 s) {
+    return {fma2(a.im, s, a.re * c), fma2(-a.re, s, a.im * c)};
+}
+template <> __device__ __forceinline__ cpx<f2> rotc<f2, true>(cpx<f2> a, f2 c, f2 s) {
+    return {fma2(-a.im, s, a.re * c), fma2(a.re, s, a.im * c)};
+}
+__device__ __forceinline__ cpx<f2> cmulc(cpx<f2> a, cpx<f2> b) {
+    return {fma2(a.im, b.im, a.re * b.re), fma2(-a.re, b.im, a.im * b.re)};
 }
 
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
@@ -228,6 +271,121 @@ template <typename T, bool INV, int R> __device__ __forceinline__ void dftR(cpx<
     else dft2<T, INV>(v);
 }
 
+// ------------------------------------------------ first pass on padded lines
+// A forward transform of a zero-padded line (Fig. 4: half of every line, more
+// on the doubled and quadrupled grids) starts from registers that are zero by
+// construction.  IEEE addition of a zero is not an identity (-0 + 0 = +0), so
+// the compiler keeps those additions; the masked forms below drop them.  Bit r
+// of the mask M says that input register r may be nonzero; every result is the
+// same value the full butterfly gives, up to the sign of a zero.
+template <bool LA, bool LB, typename T> __device__ __forceinline__ cpx<T> zadd(cpx<T> a, cpx<T> b) {
+    if constexpr (LA && LB) return a + b;
+    else if constexpr (LA) return a;
+    else if constexpr (LB) return b;
+    else return {T(0), T(0)};
+}
+template <bool LA, bool LB, typename T> __device__ __forceinline__ cpx<T> zsub(cpx<T> a, cpx<T> b) {
+    if constexpr (LA && LB) return a - b;
+    else if constexpr (LA) return a;
+    else if constexpr (LB) return {-b.re, -b.im};
+    else return {T(0), T(0)};
+}
+
+template <typename T, bool INV, unsigned M> __device__ __forceinline__ void dft4m(cpx<T>* v) {
+    constexpr bool a0 = M & 1u, a1 = M & 2u, a2 = M & 4u, a3 = M & 8u;
+    constexpr bool lp = a0 || a2, lq = a1 || a3;
+    const cpx<T> p0 = zadd<a0, a2>(v[0], v[2]), q0 = zsub<a0, a2>(v[0], v[2]);
+    const cpx<T> p1 = zadd<a1, a3>(v[1], v[3]);
+    cpx<T> q1 = zsub<a1, a3>(v[1], v[3]);
+    if constexpr (lq) q1 = rot4<T, INV>(q1);
+    v[0] = zadd<lp, lq>(p0, p1);
+    v[2] = zsub<lp, lq>(p0, p1);
+    v[1] = zadd<lp, lq>(q0, q1);
+    v[3] = zsub<lp, lq>(q0, q1);
+}
+
+// the 4 inputs v[n2], v[4+n2], v[8+n2], v[12+n2] of the first-stage DFT4 n2
+template <unsigned M, int N2> struct Grp16 {
+    static constexpr unsigned value = ((M >> N2) & 1u) | (((M >> (4 + N2)) & 1u) << 1) |
+                                      (((M >> (8 + N2)) & 1u) << 2) | (((M >> (12 + N2)) & 1u) << 3);
+};
+
+template <typename T, bool INV, unsigned M, int N2>
+__device__ __forceinline__ void dft16m_stage1(const cpx<T>* v, cpx<T>* y) {
+    cpx<T> t[4] = {v[N2], v[4 + N2], v[8 + N2], v[12 + N2]};
+    dft4m<T, INV, Grp16<M, N2>::value>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[N2 * 4 + k1] = t[k1];
+}
+
+template <typename T, bool INV, unsigned M> __device__ __forceinline__ void dft16m(cpx<T>* v) {
+    if constexpr ((M & 0xFFFFu) == 0xFFFFu) {
+        dft16<T, INV>(v);
+    } else {
+        const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+        constexpr bool g0 = Grp16<M, 0>::value != 0, g1 = Grp16<M, 1>::value != 0,
+                       g2 = Grp16<M, 2>::value != 0, g3 = Grp16<M, 3>::value != 0;
+        constexpr unsigned GL = (g0 ? 1u : 0u) | (g1 ? 2u : 0u) | (g2 ? 4u : 0u) | (g3 ? 8u : 0u);
+        cpx<T> y[16];
+        dft16m_stage1<T, INV, M, 0>(v, y);
+        dft16m_stage1<T, INV, M, 1>(v, y);
+        dft16m_stage1<T, INV, M, 2>(v, y);
+        dft16m_stage1<T, INV, M, 3>(v, y);
+        if constexpr (g1) {
+            y[5] = rotc<T, INV>(y[5], c1, s1);
+            y[6] = rot8<T, INV>(y[6]);
+            y[7] = rotc<T, INV>(y[7], s1, c1);
+        }
+        if constexpr (g2) {
+            y[9] = rot8<T, INV>(y[9]);
+            y[10] = rot4<T, INV>(y[10]);
+            y[11] = rot8_3<T, INV>(y[11]);
+        }
+        if constexpr (g3) {
+            y[13] = rotc<T, INV>(y[13], s1, c1);
+            y[14] = rot8_3<T, INV>(y[14]);
+            y[15] = rotc<T, INV>(y[15], -c1, -s1);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            cpx<T> t[4] = {y[k1], y[4 + k1], y[8 + k1], y[12 + k1]};
+            dft4m<T, INV, GL>(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+        }
+    }
+}
+
+template <typename T, bool INV, unsigned M> __device__ __forceinline__ void dft8m(cpx<T>* v) {
+    if constexpr ((M & 0xFFu) == 0xFFu) {
+        dft8<T, INV>(v);
+    } else {
+        constexpr bool b0 = M & 1u, b1 = M & 2u, b2 = M & 4u, b3 = M & 8u;
+        constexpr bool b4 = M & 16u, b5 = M & 32u, b6 = M & 64u, b7 = M & 128u;
+        constexpr unsigned UL = ((b0 || b4) ? 1u : 0u) | ((b1 || b5) ? 2u : 0u) | ((b2 || b6) ? 4u : 0u) |
+                                ((b3 || b7) ? 8u : 0u);
+        cpx<T> u[4], w[4];
+        u[0] = zadd<b0, b4>(v[0], v[4]); w[0] = zsub<b0, b4>(v[0], v[4]);
+        u[1] = zadd<b1, b5>(v[1], v[5]); w[1] = zsub<b1, b5>(v[1], v[5]);
+        u[2] = zadd<b2, b6>(v[2], v[6]); w[2] = zsub<b2, b6>(v[2], v[6]);
+        u[3] = zadd<b3, b7>(v[3], v[7]); w[3] = zsub<b3, b7>(v[3], v[7]);
+        if constexpr (b1 || b5) w[1] = rot8<T, INV>(w[1]);
+        if constexpr (b2 || b6) w[2] = rot4<T, INV>(w[2]);
+        if constexpr (b3 || b7) w[3] = rot8_3<T, INV>(w[3]);
+        dft4m<T, INV, UL>(u);
+        dft4m<T, INV, UL>(w);
+        v[0] = u[0]; v[2] = u[1]; v[4] = u[2]; v[6] = u[3];
+        v[1] = w[0]; v[3] = w[1]; v[5] = w[2]; v[7] = w[3];
+    }
+}
+
+// First pass of radix R = E with input mask M.
+template <typename T, bool INV, int R, unsigned M> __device__ __forceinline__ void dftRm(cpx<T>* v) {
+    if constexpr (R == 16) dft16m<T, INV, M>(v);
+    else if constexpr (R == 8) dft8m<T, INV, M>(v);
+    else dftR<T, INV, R>(v);
+}
+
 // Default values per thread for a line of length P.
 template <int P> struct EOf {
     static constexpr int value = P >= 16 ? 16 : 8;
@@ -273,8 +431,10 @@ __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* tw, int t) {
     return w;
 }
 
-// Passes after the first.  NS = product of the radices done so far.
-template <typename T, int P, int E, bool INV, int NS, class View>
+// Passes after the first.  NS = product of the radices done so far.  TAIL:
+// the caller writes the shared-memory line again after the transform, so the
+// last pass's reads must be complete in every thread before it returns.
+template <typename T, int P, int E, bool INV, int NS, bool TAIL, class View>
 __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
     constexpr int R = PassRadix<P, E, NS>::R;
     constexpr int NB = E / R;
@@ -285,7 +445,7 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b * R + r] = sm.ld(jj + r * (P / R));
     }
-    __syncthreads();
+    if constexpr (!LAST || TAIL) __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int jj = j + b * (P / E);
@@ -305,21 +465,25 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
             for (int r = 0; r < R; ++r) sm.st(base + r * NS, v[b * R + r]);
         }
         __syncthreads();
-        fft_rest<T, P, E, INV, NS * R>(v, j, tw, sm);
+        fft_rest<T, P, E, INV, NS * R, TAIL>(v, j, tw, sm);
     }
 }
 
 // Whole-line transform.  All threads of the CTA must call it (it contains
 // __syncthreads); the shared-memory line must not be in use by anyone else.
-template <typename T, int P, int E, bool INV, class View>
+// M: bit r set when input register r may be nonzero (all set by default).
+// TAIL = false when nobody writes the shared-memory line before the next
+// barrier of the caller (the last transform of a kernel, or one followed by
+// the caller's own barrier): the final barrier is then left out.
+template <typename T, int P, int E, bool INV, unsigned M = 0xFFFFu, bool TAIL = true, class View>
 __device__ __forceinline__ void fft_line(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
     static_assert(P >= E, "line shorter than the values a thread holds");
-    dftR<T, INV, E>(v);
+    dftRm<T, INV, E, M>(v);
     if constexpr (P > E) {
 #pragma unroll
         for (int r = 0; r < E; ++r) sm.st(E * j + r, v[r]);
         __syncthreads();
-        fft_rest<T, P, E, INV, E>(v, j, tw, sm);
+        fft_rest<T, P, E, INV, E, TAIL>(v, j, tw, sm);
     }
 }
 

@@ -83,7 +83,7 @@ __global__ void __cluster_dims__(FusedShape<T, P>::C, 1, 1) __launch_bounds__(Fu
                     v[r] = src_pair<T, TIN>(d.src[0], d.src[1], s0, s1, N, z, y, x);
                 }
             }
-            fft_line<T, P, E, false>(v, j, sm_tw,
+            fft_line<T, P, E, false, (1u << (E / 2)) - 1u>(v, j, sm_tw,
                                      LineView<T, 1, true, Log2E<E>::value>{scr + line * F::LS});
             if (valid) {
 #pragma unroll
@@ -108,7 +108,7 @@ __global__ void __cluster_dims__(FusedShape<T, P>::C, 1, 1) __launch_bounds__(Fu
                     v[r] = src[(y % F::RPC) * P + kx];
                 }
             }
-            fft_line<T, P, E, false>(v, j, sm_tw, LineView<T, F::TX, false>{scr + l});
+            fft_line<T, P, E, false, (1u << (E / 2)) - 1u>(v, j, sm_tw, LineView<T, F::TX, false>{scr + l});
 #pragma unroll
             for (int s = 0; s < E; ++s) dst[(size_t)out_index<P, E>(j, s) * P + kx] = v[s];
         }

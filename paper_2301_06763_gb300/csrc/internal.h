@@ -25,9 +25,14 @@ struct ProfScope {
 // one entry point per (precision, values per thread).  `flags`: CONV_WIDE
 // selects the wider column tile, CONV_TMA the persistent TMA-fed z-seam,
 // CONV_FUSED the cluster-fused x/y passes (level grids only; 16 values per
-// thread; sizes whose slab does not fit a cluster keep the five passes).  `dbl` selects the doubled-fine-grid geometry (16
-// values, narrow tiles only).  Returns the first launch error.
-enum { CONV_WIDE = 1, CONV_TMA = 2, CONV_FUSED = 4 };
+// thread; sizes whose slab does not fit a cluster keep the five passes),
+// CONV_PAIRED the FP32 z-seam with two columns per thread (level grids, 16
+// values per thread, P >= 64; other cases keep the classic z-seam).  `dbl`
+// selects the doubled-fine-grid geometry (16 values, narrow tiles only).
+// Returns the first launch error.
+enum { CONV_WIDE = 1, CONV_TMA = 2, CONV_FUSED = 4, CONV_PAIRED = 8 };
+// k_zseam2 over np pairs of FFT size P with TX columns per CTA (16 or 32).
+cudaError_t run_zseam_paired_f32(const ConvArgs<float>& a, int np, int P, int TX, cudaStream_t s);
 cudaError_t run_conv_f32_e16(const PairDesc<float>* pairs, int npairs, int P, bool dbl, int flags,
                              const float* spec, const cpx<float>* tw, cudaStream_t s);
 cudaError_t run_conv_f32_e8(const PairDesc<float>* pairs, int npairs, int P, bool dbl, int flags,

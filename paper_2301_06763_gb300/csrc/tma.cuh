@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(TX * P / E) k_zseam_tma(const __grid_constant_
         }
         __syncthreads();
         const LineView<T, TX, false> view{tile + l};
-        fft_line<T, P, E, false>(v, j, sm_tw, view);
+        fft_line<T, P, E, false, (1u << (E / 2)) - 1u>(v, j, sm_tw, view);
         const int fy = y <= P / 2 ? y : P - y;
         const int fx = x <= P / 2 ? x : P - x;
         const T* sp = a.spec + (size_t)fy * H + fx;
