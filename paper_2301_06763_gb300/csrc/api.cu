@@ -97,6 +97,7 @@ struct Spectrum {
     double* d64 = nullptr;
     float* d32 = nullptr;
     df* ddf = nullptr;
+    float* d32x = nullptr;   // float rows over all kx (paired FP32 z-seam), on demand
 };
 struct Twiddle {
     int dev = -1, P = 0;
@@ -166,6 +167,7 @@ static void release_spectrum(Spectrum* s) {
     cudaFree(s->d64);
     cudaFree(s->d32);
     cudaFree(s->ddf);
+    cudaFree(s->d32x);
     for (size_t i = 0; i < g_spectra.size(); ++i)
         if (g_spectra[i] == s) { g_spectra.erase(g_spectra.begin() + i); break; }
     delete s;
@@ -202,6 +204,31 @@ static nm_status build_spectrum(Spectrum* s, cudaStream_t stream) {
     if (e != cudaSuccess) return cuda_fail(e, "green spectrum");
     s->ready = true;
     return NM_OK;
+}
+
+// The float rows over all kx that the paired FP32 z-seam prefetches (built
+// once per spectrum, after the octant; synchronous on `stream`).
+static nm_status build_unfolded(Spectrum* s, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (s->d32x) return NM_OK;
+    const int N = s->N;
+    float* out = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)(N + 1) * (N + 1) * 2 * N * sizeof(float));
+    if (e == cudaSuccess) e = run_unfold_x(s->d64, out, N, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFree(out);
+        return cuda_fail(e, "unfolded spectrum");
+    }
+    s->d32x = out;
+    return NM_OK;
+}
+
+const float* unfolded_spectrum(const float* spec) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (Spectrum* s : g_spectra)
+        if (s->d32 == spec) return s->d32x;
+    return nullptr;
 }
 
 // ------------------------------------------------------------------ TMA, status
@@ -976,8 +1003,11 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
 }
 
 nm_status ensure_green(nm_plan_t p, cudaStream_t s) {
-    if (!p->spec->ready || (p->spec_dbl && !p->spec_dbl->ready) || (p->spec_qdp && !p->spec_qdp->ready))
-        return nm_green(p, (void*)s);
+    if (!p->spec->ready || (p->spec_dbl && !p->spec_dbl->ready) || (p->spec_qdp && !p->spec_qdp->ready)) {
+        nm_status st = nm_green(p, (void*)s);
+        if (st != NM_OK) return st;
+    }
+    if (p->sched.pipeline == 2 && !p->spec->d32x) return build_unfolded(p->spec, s);
     return NM_OK;
 }
 
@@ -1283,9 +1313,13 @@ nm_status nm_workspace_bytes(nm_plan_t p, size_t* bytes) {
 
 nm_status nm_spectrum_bytes(nm_plan_t p, size_t* bytes) {
     if (!p || !bytes) return fail(NM_EINVAL, "nm_spectrum_bytes: null argument");
-    size_t b = octant_count(p->N) * (sizeof(double) + sizeof(float));
-    if (p->spec_dbl) b += octant_count(2 * p->N) * (sizeof(double) + sizeof(float));
-    if (p->spec_qdp) b += octant_count(4 * p->N) * (sizeof(double) + sizeof(float));
+    // each spectrum: the octant in double, float and double-float
+    const size_t per = sizeof(double) + sizeof(float) + sizeof(df);
+    size_t b = octant_count(p->N) * per;
+    if (p->spec_dbl) b += octant_count(2 * p->N) * per;
+    if (p->spec_qdp) b += octant_count(4 * p->N) * per;
+    // float rows over all kx, for the paired FP32 z-seam (P >= 64)
+    if (p->fp32 && p->P >= 64) b += (size_t)(p->N + 1) * (p->N + 1) * p->P * sizeof(float);
     *bytes = b;
     return NM_OK;
 }

@@ -368,31 +368,46 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
 // as one transform over cpx<f2> (lane 0 = column x, lane 1 = column x + 1):
 // the twiddle and spectrum products then take half the instructions of two
 // separate float transforms, and each shared-memory access moves both lines.
-// TX columns per CTA, TX / 2 threads across them; the spectrum row of the two
-// columns is read per lane (the fold P - x runs backwards).
-// Register budget: 512 resident threads per SM (128 registers each), the
-// same 1024 lines in flight per SM as the one-column kernel.
+// TX columns per CTA, TX / 2 threads across them.  The spectrum comes as float
+// rows over all kx (specx[(fz H + fy) P + x], the octant unfolded along x):
+// the CTA's TX columns of every fz row are one aligned 4 TX-byte run, copied
+// to shared memory with asynchronous 16-byte copies issued before the column
+// loads, so they land while the forward transform runs.
 template <int NT> struct Zseam2MinBlocks {
+    // 512 resident threads per SM (128 registers each): the same 1024 lines
+    // in flight per SM as the one-column kernel
     static constexpr int value = 512 / NT > 0 ? 512 / NT : 1;
 };
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int P, int E, int TX, int GM>
 __global__ void __launch_bounds__(TX / 2 * P / E, Zseam2MinBlocks<TX / 2 * P / E>::value)
     k_zseam2(const __grid_constant__ ConvArgs<float> a) {
     using G = Geo<P, E, GM>;
     constexpr int H = P / 2 + 1, TX2 = TX / 2;
-    static_assert(TX % 2 == 0, "column pairs");
+    static_assert(TX % 4 == 0, "column pairs, 16-byte spectrum runs");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<f2>* sm_tw = reinterpret_cast<cpx<f2>*>(smem_raw);
     cpx<f2>* sm_tile = sm_tw + P;
+    float* sm_sp = reinterpret_cast<float*>(sm_tile + TX2 * P);      // [H][TX]
     const PairDesc<float>& d = a.pair[blockIdx.z];
+    const int y = blockIdx.y;
+    const int fy = y <= P / 2 ? y : P - y;
+    {
+        const float* sp = a.spec + (size_t)fy * P + blockIdx.x * TX;
+        for (int i = threadIdx.x; i < H * (TX / 4); i += blockDim.x) {
+            const int fz = i / (TX / 4), c = i % (TX / 4);
+            cp_async16(sm_sp + fz * TX + 4 * c, sp + (size_t)fz * H * P + 4 * c);
+        }
+        cp_async_commit();
+    }
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const cpx<float> w = a.tw[i];
         sm_tw[i] = {f2(w.re, w.re), f2(w.im, w.im)};
     }
     const int l = threadIdx.x % TX2, j = threadIdx.x / TX2;
     __builtin_assume(j < P / E);
-    const int y = blockIdx.y;
     const int x = blockIdx.x * TX + 2 * l;
     cpx<float>* col = d.work + (size_t)y * P + x;      // columns x, x + 1: element z at col[z * P * P]
     cpx<f2> v[E];
@@ -405,21 +420,17 @@ __global__ void __launch_bounds__(TX / 2 * P / E, Zseam2MinBlocks<TX / 2 * P / E
             v[r] = {f2(0), f2(0)};
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     const LineView<f2, TX2, false> view{sm_tile + l};
     fft_line<f2, P, E, false, G::LIVE>(v, j, sm_tw, view);
-    const int fy = y <= P / 2 ? y : P - y;
-    const int fx0 = x <= P / 2 ? x : P - x;
-    const int fx1 = x + 1 <= P / 2 ? x + 1 : P - x - 1;
-    const float* sp = a.spec + (size_t)fy * H;
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const int kz = out_index<P, E>(j, s);
         const int fz = kz <= P / 2 ? kz : P - kz;
-        const float* row = sp + (size_t)fz * H * H;
-        const f2 g(__ldg(row + fx0), __ldg(row + fx1));
-        v[s].re *= g;
-        v[s].im *= g;
+        const float2 g = *reinterpret_cast<const float2*>(sm_sp + fz * TX + 2 * l);
+        v[s].re *= f2(g.x, g.y);
+        v[s].im *= f2(g.x, g.y);
     }
     seam_permute<f2, P, E>(v);
     fft_line<f2, P, E, true, 0xFFFFu, false>(v, j, sm_tw, view);

@@ -1,17 +1,28 @@
 // conv_f32_pair.cu -- the FP32 z-seam with two columns per thread (k_zseam2),
 // level grids, 16 values per thread, for both column-tile widths.
+#include <mutex>
+
 #include "internal.h"
 
 namespace nm {
 
 template <int P, int TX>
 static cudaError_t launch_zseam2(const ConvArgs<float>& a, int np, cudaStream_t s) {
-    constexpr int E = 16, NT = TX / 2 * P / E;
-    const size_t smem = (size_t)P * sizeof(cpx<f2>) + (size_t)(TX / 2) * P * sizeof(cpx<f2>);
+    constexpr int E = 16, NT = TX / 2 * P / E, H = P / 2 + 1;
+    const size_t smem = (size_t)P * sizeof(cpx<f2>) + (size_t)(TX / 2) * P * sizeof(cpx<f2>) +
+                        (size_t)H * TX * sizeof(float);
     static const cudaError_t prep =
         cudaFuncSetAttribute(k_zseam2<P, E, TX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (prep != cudaSuccess) return prep;
-    k_zseam2<P, E, TX, 0><<<dim3(P / TX, P, np), NT, smem, s>>>(a);
+    // the kernel reads the spectrum as float rows over all kx
+    const float* specx = unfolded_spectrum(a.spec);
+    if (!specx) return cudaErrorInvalidValue;
+    static ConvArgs<float> b;   // host staging of the (large) parameter block
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    b = a;
+    b.spec = specx;
+    k_zseam2<P, E, TX, 0><<<dim3(P / TX, P, np), NT, smem, s>>>(b);
     return cudaGetLastError();
 }
 

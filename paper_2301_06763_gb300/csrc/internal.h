@@ -65,6 +65,11 @@ int sm_count();
 cudaError_t run_green_octant(double* out, double* scratch, const double* ctab, int N,
                              double self_term, cudaStream_t s);
 cudaError_t run_to_float(const double* in, float* out, size_t n, cudaStream_t s);
+// The octant ((N+1)^3 doubles) as float rows over all 2N kx: (N+1)^2 2N floats.
+cudaError_t run_unfold_x(const double* in, float* out, int N, cudaStream_t s);
+// The unfolded float spectrum that belongs to the float octant `spec` (built
+// by the plan before its first paired z-seam), or null.
+const float* unfolded_spectrum(const float* spec);
 cudaError_t run_to_df(const double* in, df* out, size_t n, cudaStream_t s);
 
 // Restriction of level m+1 onto level m's covered cells (mean of 2^3 children).

@@ -176,6 +176,27 @@ __global__ void k_to_df(const double* __restrict__ in, df* __restrict__ out, siz
         out[i] = df_from_double(in[i]);
 }
 
+// The octant S[fz][fy][fx] (fx <= N) as float rows over the whole kx range:
+// out[(fz H + fy) P + x] = S[fz][fy][x <= N ? x : P - x], so that the kx
+// columns of one z-seam tile are contiguous and 16-byte aligned.
+__global__ void k_unfold_x(const double* __restrict__ in, float* __restrict__ out, int N) {
+    const int H = N + 1, P = 2 * N;
+    const size_t n = (size_t)H * H * P;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % P);
+        const size_t row = i / P;
+        out[i] = (float)in[row * H + (x <= N ? x : P - x)];
+    }
+}
+
+cudaError_t run_unfold_x(const double* in, float* out, int N, cudaStream_t s) {
+    const size_t n = (size_t)(N + 1) * (N + 1) * 2 * N;
+    const int blocks = (int)((n + 255) / 256 < 152 * 32 ? (n + 255) / 256 : 152 * 32);
+    k_unfold_x<<<blocks, 256, 0, s>>>(in, out, N);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t run_to_df(const double* in, df* out, size_t n, cudaStream_t s) {
     const int blocks = (int)((n + 255) / 256 < 152 * 32 ? (n + 255) / 256 : 152 * 32);
     k_to_df<<<blocks, 256, 0, s>>>(in, out, n);

@@ -79,3 +79,19 @@ def test_paired_zseam_schedule_limits():
         p.set_schedule(2, 16, 1, 2, 0)
         r = torch.zeros((2, 32, 32, 32), dtype=torch.float32, device="cuda")
         assert float(p.potential(r).abs().max()) == 0.0
+
+
+def test_paired_after_one_column_on_one_plan():
+    # the spectrum rows over all kx are built when a plan first solves with
+    # the paired z-seam, also after solves with the one-column kernel
+    import torch
+    m = nm()
+    L, N = 3, 64
+    rho = torch.from_numpy(wl.random_density(2, L, N)).to("cuda", torch.float32)
+    with m.Plan(L, N, 1.0 / N, precision="fp32") as p:
+        p.set_schedule(L, 16, 0, 0, 0)
+        one = p.potential(rho).cpu().numpy()
+        p.set_schedule(L, 16, 0, 2, 0)
+        two = p.potential(rho).cpu().numpy()
+        assert p.spectrum_bytes() >= (N + 1) ** 3 * 20 + (N + 1) ** 2 * 2 * N * 4
+    assert rel_l2(two, one) <= 1e-6
