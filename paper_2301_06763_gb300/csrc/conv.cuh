@@ -59,9 +59,12 @@ template <typename T> struct ConvArgs {
     const cpx<T>* tw;       // twiddle table, P entries
 };
 
-template <typename T>
-__device__ __forceinline__ void load_twiddles(cpx<T>* sm_tw, const cpx<T>* tw, int P) {
-    for (int i = threadIdx.x; i < P; i += blockDim.x) sm_tw[i] = tw[i];
+// Stage the twiddles of a size-P line transform with E values per thread:
+// the plain table (P entries), or with PT in the per-pass order (P - E).
+template <int P, int E, bool PT = false, typename T>
+__device__ __forceinline__ void load_twiddles(cpx<T>* sm_tw, const cpx<T>* tw) {
+    if constexpr (PT) fill_pass_twiddles<P, E>(sm_tw, [&](int t) { return tw[t]; });
+    else for (int i = threadIdx.x; i < P; i += blockDim.x) sm_tw[i] = tw[i];
 }
 
 // Density of a real field at block cell (z, y, x), already scaled.  All in
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
     const PairDesc<T>& d = a.pair[blockIdx.y];
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E, true>(sm_tw, a.tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int row0 = blockIdx.x * LINES;
     const int row = row0 + line;
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
         }
     }
     __syncthreads();
-    fft_line<T, P, E, false, G::LIVE, false>(v, j, sm_tw,
+    fft_line<T, P, E, false, G::LIVE, false, true>(v, j, sm_tw,
                                              LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
     if (valid) {
         cpx<T>* dst = d.work + ((size_t)(zi + G::OFF) * P + (yi + G::OFF)) * P;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvA
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
     TIN* stage = reinterpret_cast<TIN*>(sm_lines + LINES * (P + P / E));   // [2][TILE]
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E, true>(sm_tw, a.tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int total = npairs * TILES;
     auto issue = [&](int t, int b) {
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvA
                 v[r].im = (hole && !cov) ? val * s1 : T(0);
             }
         }
-        fft_line<T, P, E, false, G::LIVE, false>(v, j, sm_tw,
+        fft_line<T, P, E, false, G::LIVE, false, true>(v, j, sm_tw,
                                                  LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
         cpx<T>* out = d.work + ((size_t)zi * P + yi) * P;
 #pragma unroll
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
     const PairDesc<T>& d = a.pair[blockIdx.z];
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E>(sm_tw, a.tw);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
     // blockDim.x = TX P/E: lets the compiler see which outputs of the last
     // pass the window keeps, and drop the rest
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
     const PairDesc<T>& d = a.pair[blockIdx.z];
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E, true>(sm_tw, a.tw);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
     // blockDim.x = TX P/E: lets the compiler see which outputs of the last
     // pass the window keeps, and drop the rest
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
     }
     __syncthreads();
     const LineView<T, TX, false> view{sm_tile + l};
-    fft_line<T, P, E, false, G::LIVE>(v, j, sm_tw, view);
+    fft_line<T, P, E, false, G::LIVE, true, true>(v, j, sm_tw, view);
     const int fy = y <= P / 2 ? y : P - y;
     const int fx = x <= P / 2 ? x : P - x;
     const T* sp = a.spec + (size_t)fy * H + fx;
@@ -355,7 +358,7 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
         v[s].im *= g;
     }
     seam_permute<T, P, E>(v);
-    fft_line<T, P, E, true, 0xFFFFu, false>(v, j, sm_tw, view);
+    fft_line<T, P, E, true, 0xFFFFu, false, true>(v, j, sm_tw, view);
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const int e = out_index<P, E>(j, s);
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
     const PairDesc<T>& d = a.pair[blockIdx.y];
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E, true>(sm_tw, a.tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int row = blockIdx.x * LINES + line;
     const bool valid = row < HALF * HALF;
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = valid ? src[j + r * (P / E)] : cpx<T>{T(0), T(0)};
     __syncthreads();
-    fft_line<T, P, E, true, 0xFFFFu, false>(v, j, sm_tw,
+    fft_line<T, P, E, true, 0xFFFFu, false, true>(v, j, sm_tw,
                                             LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
     if (valid) {
 #pragma unroll

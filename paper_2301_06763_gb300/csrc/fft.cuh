@@ -19,7 +19,8 @@
 //
 // Forward: X[k] = sum_j x[j] exp(-2 pi i jk/P); inverse: the + sign, no 1/P.
 // Twiddles come from a table tw[t] = exp(-2 pi i t / P) built on the host in
-// double precision (std::cos / std::sin) and staged in shared memory.
+// double precision (std::cos / std::sin) and staged in shared memory, as is
+// or in the per-pass order of fill_pass_twiddles.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -431,10 +432,29 @@ __device__ __forceinline__ cpx<T> twiddle(const cpx<T>* tw, int t) {
     return w;
 }
 
+// Twiddle table of the passes after the first, pass by pass: the pass that
+// starts at stride NS (radix R) multiplies value r of butterfly k by
+// w^(k r P/(NS R)), w = exp(-2 pi i/P), kept at [NS - E + (r - 1) NS + k]
+// (r = 1..R-1, k < NS; P - E entries in all).  The threads of one line read
+// consecutive k there, which fall in distinct shared-memory banks; in the
+// plain table w^t an even r puts the k of a row kernel's warp (16 threads
+// of one line) on a few banks.  `w(t)` returns w^t in the table's type.
+template <int P, int E, int NS = E, class C, class F>
+__device__ __forceinline__ void fill_pass_twiddles(C* out, const F& w) {
+    if constexpr (NS < P) {
+        constexpr int R = PassRadix<P, E, NS>::R;
+        for (int i = threadIdx.x; i < (R - 1) * NS; i += blockDim.x) {
+            const int r = i / NS + 1, k = i % NS;
+            out[NS - E + i] = w(k * r * (P / (NS * R)));
+        }
+        fill_pass_twiddles<P, E, NS * R>(out, w);
+    }
+}
+
 // Passes after the first.  NS = product of the radices done so far.  TAIL:
 // the caller writes the shared-memory line again after the transform, so the
 // last pass's reads must be complete in every thread before it returns.
-template <typename T, int P, int E, bool INV, int NS, bool TAIL, class View>
+template <typename T, int P, int E, bool INV, int NS, bool TAIL, bool PT, class View>
 __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
     constexpr int R = PassRadix<P, E, NS>::R;
     constexpr int NB = E / R;
@@ -452,7 +472,8 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
         const int k = jj & (NS - 1);
 #pragma unroll
         for (int r = 1; r < R; ++r)
-            v[b * R + r] = cmul(v[b * R + r], twiddle<T, INV>(tw, k * r * (P / (NS * R))));
+            v[b * R + r] = cmul(v[b * R + r], twiddle<T, INV>(tw, PT ? NS - E + (r - 1) * NS + k
+                                                                      : k * r * (P / (NS * R))));
         dftR<T, INV, R>(&v[b * R]);
     }
     if constexpr (!LAST) {
@@ -465,7 +486,7 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
             for (int r = 0; r < R; ++r) sm.st(base + r * NS, v[b * R + r]);
         }
         __syncthreads();
-        fft_rest<T, P, E, INV, NS * R, TAIL>(v, j, tw, sm);
+        fft_rest<T, P, E, INV, NS * R, TAIL, PT>(v, j, tw, sm);
     }
 }
 
@@ -474,8 +495,10 @@ __device__ __forceinline__ void fft_rest(cpx<T>* v, int j, const cpx<T>* tw, con
 // M: bit r set when input register r may be nonzero (all set by default).
 // TAIL = false when nobody writes the shared-memory line before the next
 // barrier of the caller (the last transform of a kernel, or one followed by
-// the caller's own barrier): the final barrier is then left out.
-template <typename T, int P, int E, bool INV, unsigned M = 0xFFFFu, bool TAIL = true, class View>
+// the caller's own barrier): the final barrier is then left out.  PT: the
+// twiddles are in the per-pass order of fill_pass_twiddles (else the plain
+// table tw[t] = w^t); each kernel takes the order measured faster for it.
+template <typename T, int P, int E, bool INV, unsigned M = 0xFFFFu, bool TAIL = true, bool PT = false, class View>
 __device__ __forceinline__ void fft_line(cpx<T>* v, int j, const cpx<T>* tw, const View& sm) {
     static_assert(P >= E, "line shorter than the values a thread holds");
     dftRm<T, INV, E, M>(v);
@@ -483,7 +506,7 @@ __device__ __forceinline__ void fft_line(cpx<T>* v, int j, const cpx<T>* tw, con
 #pragma unroll
         for (int r = 0; r < E; ++r) sm.st(E * j + r, v[r]);
         __syncthreads();
-        fft_rest<T, P, E, INV, E, TAIL>(v, j, tw, sm);
+        fft_rest<T, P, E, INV, E, TAIL, PT>(v, j, tw, sm);
     }
 }
 

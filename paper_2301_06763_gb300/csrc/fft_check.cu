@@ -13,12 +13,12 @@ __global__ void __launch_bounds__(256) k_fft_lines(cpx<T>* data, int lines) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
-    // twiddles exp(-2 pi i t / P) in double, rounded to T
-    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    // twiddles exp(-2 pi i t / P) in double, rounded to T, in per-pass order
+    fill_pass_twiddles<P, E>(sm_tw, [](int t) {
         double s, c;
         sincospi(2.0 * (double)t / (double)P, &s, &c);
-        sm_tw[t] = {(T)c, (T)-s};
-    }
+        return cpx<T>{(T)c, (T)-s};
+    });
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int l = blockIdx.x * LINES + line;
     const bool valid = l < lines;
@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(256) k_fft_lines(cpx<T>* data, int lines) {
 #pragma unroll
     for (int r = 0; r < E; ++r) v[r] = valid ? src[j + r * (P / E)] : cpx<T>{T(0), T(0)};
     __syncthreads();
-    fft_line<T, P, E, INV>(v, j, sm_tw, LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
+    fft_line<T, P, E, INV, 0xFFFFu, true, true>(v, j, sm_tw,
+                                                LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
     if (valid) {
 #pragma unroll
         for (int s = 0; s < E; ++s) src[out_index<P, E>(j, s)] = v[s];

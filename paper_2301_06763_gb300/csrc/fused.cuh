@@ -64,7 +64,7 @@ __global__ void __cluster_dims__(FusedShape<T, P>::C, 1, 1) __launch_bounds__(Fu
     const int rank = (int)cluster.block_rank();
     const int z = blockIdx.x / C;
     const PairDesc<T>& d = a.pair[blockIdx.y];
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E>(sm_tw, a.tw);
     const T s0 = (T)d.src[0].scale, s1 = (T)d.src[1].scale;
     __syncthreads();
     // phase 1: rows along x
@@ -130,7 +130,7 @@ __global__ void __cluster_dims__(FusedShape<T, P>::C, 1, 1) __launch_bounds__(Fu
     const int rank = (int)cluster.block_rank();
     const int z = blockIdx.x / C;
     const PairDesc<T>& d = a.pair[blockIdx.y];
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E>(sm_tw, a.tw);
     __syncthreads();
     // phase 1: columns along y (inverse), keep y < N
     {

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(TX * P / E) k_zseam_tma(const __grid_constant_
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    load_twiddles(sm_tw, a.tw, P);
+    load_twiddles<P, E>(sm_tw, a.tw);
     __syncthreads();
     // loads issued and not yet consumed, with the phase parity each completes
     // (tracked by thread 0, the only thread that issues copies)
