@@ -216,27 +216,40 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Staged density rows of k_xfwd_pipe: LINES rows of NIN values, each row
+// padded by 64 bytes so that the two rows a warp reads (16 threads each) start
+// half a bank cycle apart.
+template <typename TIN, int P, int E> struct XfwdStage {
+    static constexpr int LINES = 256 / (P / E), NIN = P / 2;
+    static constexpr int PITCH = NIN + 64 / (int)sizeof(TIN);
+    static constexpr int ELEMS = LINES * PITCH;       // one of the two buffers
+};
+
 template <typename T, typename TIN, int P, int E>
 __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvArgs<T> a, int npairs) {
     using G = Geo<P, E, 0>;
+    using S = XfwdStage<TIN, P, E>;
     constexpr int TPL = P / E, LINES = 256 / TPL, NIN = G::NIN;
     constexpr int TILE = LINES * NIN;                 // density values per tile
     constexpr int TILES = NIN * NIN / LINES;          // tiles per pair
     constexpr int VEC = 16 / sizeof(TIN);
-    static_assert((NIN * NIN) % LINES == 0 && TILE % (256 * VEC) == 0, "tile shape");
+    static_assert((NIN * NIN) % LINES == 0 && TILE % (256 * VEC) == 0 && NIN % VEC == 0, "tile shape");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
-    TIN* stage = reinterpret_cast<TIN*>(sm_lines + LINES * (P + P / E));   // [2][TILE]
+    TIN* stage = reinterpret_cast<TIN*>(sm_lines + LINES * (P + P / E));   // [2][LINES][PITCH]
     load_twiddles<P, E, true>(sm_tw, a.tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int total = npairs * TILES;
     auto issue = [&](int t, int b) {
         const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
         const TIN* src = (const TIN*)a.pair[pr].src[0].rho + (size_t)row0 * NIN;
-        TIN* dst = stage + b * TILE;
+        TIN* dst = stage + b * S::ELEMS;
 #pragma unroll
-        for (int i = threadIdx.x * VEC; i < TILE; i += 256 * VEC) cp_async16(dst + i, src + i);
+        for (int i = threadIdx.x * VEC; i < TILE; i += 256 * VEC) {
+            const int row = i / NIN;
+            cp_async16(dst + row * S::PITCH + (i - row * NIN), src + i);
+        }
     };
     int t = blockIdx.x;
     if (t < total) issue(t, 0);
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvA
         const int q = NIN / 4, h = NIN / 2;
         const bool row_cov = (unsigned)(zi - q) < (unsigned)h && (unsigned)(yi - q) < (unsigned)h;
         const bool hole = d.src[1].mode == SRC_HOLE;
-        const TIN* st = stage + (k & 1) * TILE + line * NIN;
+        const TIN* st = stage + (k & 1) * S::ELEMS + line * S::PITCH;
         cpx<T> v[E];
 #pragma unroll
         for (int r = 0; r < E; ++r) {

@@ -142,8 +142,7 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
                        (d.src[1].mode == SRC_NONE || (d.src[1].mode == SRC_HOLE && d.src[1].rho == d.src[0].rho));
             }
             if (pipe) {
-                constexpr int TILE = LINES * Gm::NIN;
-                const size_t sm_p = sm_x + 2 * (size_t)TILE * sizeof(TIN);
+                const size_t sm_p = sm_x + 2 * (size_t)XfwdStage<TIN, P, E>::ELEMS * sizeof(TIN);
                 static int occ = -1;
                 static const cudaError_t prep_p = [&]() {
                     cudaError_t e = prep_kernel(k_xfwd_pipe<T, TIN, P, E>, sm_p);
