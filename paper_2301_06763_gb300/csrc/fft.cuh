@@ -79,8 +79,8 @@ __device__ __forceinline__ cpx<df> operator-(cpx<df> a, cpx<df> b) {
 // complex value of type cpx<f2> carries the same element of two lines and
 // every step of the transform (sums, twiddle products, scaling) acts on both
 // lines with one paired instruction.  With the twiddles broadcast to both
-// lanes, a complex product costs 2 paired multiply-adds per line pair where
-// cpx<float> needs 4 scalar ones per line.
+// lanes, a complex product costs 4 paired instructions (2 FMUL2, 2 FFMA2) for
+// the two lines, where cpx<float> needs 4 scalar ones for each line.
 struct alignas(8) f2 {
     float x, y;
     f2() = default;
@@ -172,9 +172,6 @@ template <> __device__ __forceinline__ cpx<f2> rotc<f2, false>(cpx<f2> a, f2 c, 
 }
 template <> __device__ __forceinline__ cpx<f2> rotc<f2, true>(cpx<f2> a, f2 c, f2 s) {
     return {fma2(-a.im, s, a.re * c), fma2(a.re, s, a.im * c)};
-}
-__device__ __forceinline__ cpx<f2> cmulc(cpx<f2> a, cpx<f2> b) {
-    return {fma2(a.im, b.im, a.re * b.re), fma2(-a.re, b.im, a.im * b.re)};
 }
 
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
