@@ -144,9 +144,16 @@ def pass_bytes(name, N, fp32):
 
 
 def source_hash():
+    """First 16 hex digits of the sha256 of the sources that define the
+    measured passes' kernels, with comments and white space taken out (a
+    comment edit leaves the kernels, and so their measured traffic, as they
+    were)."""
     h = hashlib.sha256()
-    for f in ("fft.cuh", "conv.cuh", "conv_inst.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2301_06763_gb300", "csrc", f), "rb").read())
+    for f in ("fft.cuh", "conv.cuh", "conv_inst.cuh", "conv_f32_pair.cu", "support.cu"):
+        text = open(os.path.join(ROOT, "paper_2301_06763_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -384,9 +384,10 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
 // as one transform over cpx<f2> (lane 0 = column x, lane 1 = column x + 1):
 // the twiddle and spectrum products then take half the instructions of two
 // separate float transforms, and each shared-memory access moves both lines.
-// TX columns per CTA, TX / 2 threads across them.  The spectrum comes as float
-// rows over all kx (specx[(fz H + fy) P + x], the octant unfolded along x):
-// the CTA's TX columns of every fz row are one aligned 4 TX-byte run, copied
+// TX columns per CTA, TX / 2 threads across them.  Here a.spec holds float
+// rows over all kx, a.spec[(fz H + fy) P + x] = octant[fz][fy][fold(x)] (the
+// launcher passes them in place of the octant): the CTA's TX columns of every
+// fz row are one aligned 4 TX-byte run, copied
 // to shared memory with asynchronous 16-byte copies issued before the column
 // loads, so they land while the forward transform runs.
 template <int NT> struct Zseam2MinBlocks {
