@@ -11,9 +11,11 @@ static cudaError_t launch_zseam2(const ConvArgs<float>& a, int np, cudaStream_t 
     constexpr int E = 16, NT = TX / 2 * P / E, H = P / 2 + 1;
     const size_t smem = (size_t)P * sizeof(cpx<f2>) + (size_t)(TX / 2) * P * sizeof(cpx<f2>) +
                         (size_t)H * TX * sizeof(float);
-    static const cudaError_t prep =
-        cudaFuncSetAttribute(k_zseam2<P, E, TX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (prep != cudaSuccess) return prep;
+    static PerDevice<cudaError_t> prep;   // the shared-memory limit, once per device
+    const cudaError_t pe = prep.get(current_device(), [&]() {
+        return cudaFuncSetAttribute(k_zseam2<P, E, TX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }, cudaErrorInvalidDevice);
+    if (pe != cudaSuccess) return pe;
     // the kernel reads the spectrum as float rows over all kx
     const float* specx = unfolded_spectrum(a.spec);
     if (!specx) return cudaErrorInvalidValue;

@@ -21,14 +21,17 @@ static cudaError_t zseam_tma(const ConvArgs<T>& a, int np, cudaStream_t s) {
     constexpr int NT = TX * P / E;
     const size_t c = sizeof(cpx<T>);
     const size_t smem = 2 * (size_t)P * TX * c + (size_t)P * c + 2 * sizeof(uint64_t);
-    static int occ = -1;   // resident CTAs per SM, computed once per kernel
-    static const cudaError_t prepared = [&]() {
-        cudaError_t e = prep_kernel(k_zseam_tma<T, P, E, TX>, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zseam_tma<T, P, E, TX>, NT, smem);
-        return e;
-    }();
-    if (prepared != cudaSuccess) return prepared;
+    // shared-memory limit and resident CTAs per SM, once per device
+    static PerDevice<KernelPrep> prep;
+    const KernelPrep kp = prep.get(current_device(), [&]() {
+        KernelPrep r;
+        r.err = prep_kernel(k_zseam_tma<T, P, E, TX>, smem);
+        if (r.err == cudaSuccess)
+            r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.occ, k_zseam_tma<T, P, E, TX>, NT, smem);
+        return r;
+    }, KernelPrep{cudaErrorInvalidDevice, 0});
+    if (kp.err != cudaSuccess) return kp.err;
+    const int occ = kp.occ;
     static TmaArgs<T> ta;   // host staging of the (large) parameter block
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
@@ -54,11 +57,12 @@ static cudaError_t zseam_tma(const ConvArgs<T>& a, int np, cudaStream_t s) {
 template <typename T, int P>
 static cudaError_t fused_pass(const ConvArgs<T>& a, int np, bool fwd, cudaStream_t s) {
     using F = FusedShape<T, P>;
-    static const cudaError_t prepared = [&]() {
+    static PerDevice<cudaError_t> prep;
+    const cudaError_t prepared = prep.get(current_device(), [&]() {
         cudaError_t e = prep_kernel(k_xyfwd<T, T, P>, F::SMEM);
         if (e == cudaSuccess) e = prep_kernel(k_yxinv<T, P>, F::SMEM_INV);
         return e;
-    }();
+    }, cudaErrorInvalidDevice);
     if (prepared != cudaSuccess) return prepared;
     const dim3 grid(F::N * F::C, np);
     if (fwd) k_xyfwd<T, T, P><<<grid, F::NT, F::SMEM, s>>>(a);
@@ -89,8 +93,11 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
                 } else {
                     constexpr int NT = TX * P / E;
                     const size_t sm_yz = (size_t)P * sizeof(cpx<T>) + (size_t)TX * P * sizeof(cpx<T>);
-                    static const cudaError_t prep = prep_kernel(k_zseam<T, P, E, TX, false>, sm_yz);
-                    if (prep != cudaSuccess) return prep;
+                    static PerDevice<cudaError_t> prep;
+                    const cudaError_t pe = prep.get(current_device(), [&]() {
+                        return prep_kernel(k_zseam<T, P, E, TX, false>, sm_yz);
+                    }, cudaErrorInvalidDevice);
+                    if (pe != cudaSuccess) return pe;
                     k_zseam<T, P, E, TX, false><<<dim3(P / TX, P, np), NT, sm_yz, s>>>(a);
                 }
             }
@@ -112,15 +119,16 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
     const size_t c = sizeof(cpx<T>);
     const size_t sm_x = (size_t)P * c + (size_t)LINES * (P + P / E) * c;
     const size_t sm_yz = (size_t)P * c + (size_t)TX * P * c;
-    // shared-memory limits are set once per kernel (thread-safe static init)
-    static const cudaError_t prepared = [&]() {
+    // shared-memory limits are set once per kernel and device
+    static PerDevice<cudaError_t> prep;
+    const cudaError_t prepared = prep.get(current_device(), [&]() {
         cudaError_t e;
         if ((e = prep_kernel(k_xfwd<T, TIN, P, E, GM>, sm_x)) != cudaSuccess) return e;
         if ((e = prep_kernel(k_ypass<T, P, E, TX, false, GM>, sm_yz)) != cudaSuccess) return e;
         if ((e = prep_kernel(k_zseam<T, P, E, TX, GM>, sm_yz)) != cudaSuccess) return e;
         if ((e = prep_kernel(k_ypass<T, P, E, TX, true, GM>, sm_yz)) != cudaSuccess) return e;
         return prep_kernel(k_xinv<T, P, E, GM>, sm_x);
-    }();
+    }, cudaErrorInvalidDevice);
     if (prepared != cudaSuccess) return prepared;
     const int rows_in = Gm::NIN * Gm::NIN;
     const int rows_out = Gm::NOUT * Gm::NOUT;
@@ -143,14 +151,17 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
             }
             if (pipe) {
                 const size_t sm_p = sm_x + 2 * (size_t)XfwdStage<TIN, P, E>::ELEMS * sizeof(TIN);
-                static int occ = -1;
-                static const cudaError_t prep_p = [&]() {
-                    cudaError_t e = prep_kernel(k_xfwd_pipe<T, TIN, P, E>, sm_p);
-                    if (e == cudaSuccess)
-                        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xfwd_pipe<T, TIN, P, E>, 256, sm_p);
-                    return e;
-                }();
-                if (prep_p != cudaSuccess) return prep_p;
+                static PerDevice<KernelPrep> prep_p;
+                const KernelPrep kp = prep_p.get(current_device(), [&]() {
+                    KernelPrep r;
+                    r.err = prep_kernel(k_xfwd_pipe<T, TIN, P, E>, sm_p);
+                    if (r.err == cudaSuccess)
+                        r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.occ, k_xfwd_pipe<T, TIN, P, E>, 256,
+                                                                              sm_p);
+                    return r;
+                }, KernelPrep{cudaErrorInvalidDevice, 0});
+                if (kp.err != cudaSuccess) return kp.err;
+                const int occ = kp.occ;
                 const int tiles = np * (rows_in / LINES);
                 int grid = (occ > 0 ? occ : 1) * sm_count();
                 if (grid > tiles) grid = tiles;

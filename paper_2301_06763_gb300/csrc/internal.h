@@ -4,9 +4,22 @@
 #include <stdint.h>
 
 #include "conv.cuh"
+#include "per_device.h"
 #include "tma.cuh"
 
 namespace nm {
+
+// The calling thread's current device, or -1.
+inline int current_device() {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+// Per-device set-up of one kernel: the error of setting its attributes, and
+// its resident CTAs per SM where the launcher needs them.
+struct KernelPrep {
+    cudaError_t err = cudaSuccess;
+    int occ = 0;
+};
 
 // Counts every kernel launched by the library (reported by nm_kernel_launches).
 void count_launches(int n);
