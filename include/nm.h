@@ -21,9 +21,15 @@
  *
  * Levels are combined as in Sect. 4 (Fig. 5, Eq. 14):
  *     Phi(Omega^n) = Phi^n + sum_{k<n} interp_{k->n}(Phi^k_hole)
- * where Phi^k_hole is level k's potential with the covered cells' mass removed
- * and interp is trilinear interpolation from level-k cell centres straight to
- * level-n cell centres.  With NM_METHOD_DIPOLE_PAIR the pairwise dipole
+ * where Phi^k_hole is level k's potential with the covered cells' mass
+ * removed.  By default (NM_INTERP_DIAGONAL) the coarser holes reach level n
+ * through the two-point rule of Eqs. 3-6 applied one level at a time:
+ *     carry_n = D(carry_{n-1} + Phi^{n-1}_hole),  carry_1 = D(Phi^0_hole),
+ *     Phi(Omega^n) = Phi^n + carry_n,
+ * with D(f) at a fine centre = 3/4 f(nearest coarse centre) + 1/4 f(its
+ * diagonal neighbour towards the fine centre).  NM_INTERP_TRILINEAR instead
+ * interpolates each Phi^k_hole trilinearly from level-k centres straight to
+ * level-n centres (see nm_options.interp).  With NM_METHOD_DIPOLE_PAIR the pairwise dipole
  * method of Sect. 7 and Appendix B (Eqs. 15, B.1-B.2) is used instead for
  * every level but the finest:
  *     Phi(Omega^n) = Phi^n_hole + reduce(Phi^{n+1}_dbl) + sum_{k<n} interp(Phi^k_hole)
@@ -310,15 +316,17 @@ nm_status nm_profile_read(nm_kernel_stat* out, int max, int* count);
  * their device pools at start-up and forbid later allocations, processes whose
  * device memory belongs to another framework's allocator, and loops that
  * cannot afford cudaMalloc's implicit device-wide synchronisation.
- * It computes the same potential as nm_potential (original method, Eq. 14) for
- * the mesh described by `opt` (method must be NM_METHOD_ORIGINAL, else
- * NM_EUNSUPPORTED; either interpolation), from device
- * `rho` to device `phi`, asynchronously on `stream`, and never allocates: all
- * scratch (spectrum, tables, work buffer, level potentials) lives in one
- * file-scope device array of NM_NOALLOC_SCRATCH_BYTES that every GPU loading
- * the library holds until exit.  Meshes whose scratch would not fit are
- * rejected with NM_EINVAL and a message giving the bytes needed (N <= 32 fits
- * for every level count in FP32 and up to 15 levels in FP64; N = 64 does not).
+ * It computes the same potential as nm_potential with a plan made from `opt`
+ * for the mesh described by `opt` (method must be NM_METHOD_ORIGINAL, else
+ * NM_EUNSUPPORTED; precision NM_FP64 or NM_FP32; either interpolation), from
+ * device `rho` to device `phi`, asynchronously on `stream`, and never
+ * allocates: all scratch (spectrum, tables, work buffer, level potentials)
+ * lives in one file-scope device array of NM_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until exit.  Meshes whose scratch would not
+ * fit are rejected with NM_EINVAL and a message giving the bytes needed.
+ * What fits: N <= 16, every level count, both precisions; N = 32 in FP32,
+ * every level count; N = 32 in FP64, up to 14 levels with NM_INTERP_DIAGONAL
+ * and up to 15 with NM_INTERP_TRILINEAR; N >= 64 never.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before
  * any stream capture.  All calls share the array and it keeps the last call's

@@ -169,7 +169,7 @@ extern "C" nm_status nm_potential_noalloc(const nm_options* opt, const void* rho
     if (o.precision == NM_FP64X)
         return record_error(NM_EUNSUPPORTED, "nm_potential_noalloc: NM_FP64X is not built here");
     if (o.method != NM_METHOD_ORIGINAL)
-        return record_error(NM_EUNSUPPORTED, "nm_potential_noalloc: only the original method (Eq. 14)");
+        return record_error(NM_EUNSUPPORTED, "nm_potential_noalloc: only NM_METHOD_ORIGINAL is built here");
     const bool fp32 = o.precision == NM_FP32;
     const Layout lay = carve(o.levels, o.N <= 256 ? o.N : 256, fp32, o.interp == NM_INTERP_DIAGONAL);
     if (o.N > 256 || lay.total > kScratchBytes) {

@@ -65,11 +65,48 @@ def test_matches_allocating_entry_point_on_consecutive_calls(precision, interp):
             assert rel_l2(a, b) <= FP32_REL_L2 and rel_max(a, b) <= FP32_REL_MAX
 
 
-def test_rejects_meshes_beyond_the_static_maximum():
+# the extremes of what the fixed array accepts: one level (no restricted
+# densities, hole crops or carried holes at all), and the largest FP64 meshes
+# of N = 32 that fit with each interpolation (the diagonal rule's carried
+# holes need room that the trilinear rule does not, so trilinear fits one
+# level more)
+@pytest.mark.parametrize("L,N,precision,interp", [
+    (1, 16, "fp64", "diagonal"), (1, 32, "fp32", "diagonal"), (1, 32, "fp64", "trilinear"),
+    (14, 32, "fp64", "diagonal"), (15, 32, "fp64", "trilinear"), (16, 32, "fp32", "diagonal"),
+])
+def test_matches_allocating_entry_point_at_the_limits(L, N, precision, interp):
     import torch
     m = nm()
-    rho = torch.zeros((2, 64, 64, 64), dtype=torch.float64, device="cuda")
-    phi = torch.empty_like(rho)
-    st = noalloc(options(2, 64, 1 / 64, "fp64"), rho, phi)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    dx0 = 0.8 / N
+    with m.Plan(L, N, dx0, 1.3, precision=precision, interp=interp) as plan:
+        for seed in (11, 12):      # two calls in a row on the same array
+            rho = torch.from_numpy(wl.random_density(seed, L, N)).to("cuda", dt)
+            ref = plan.potential(rho)
+            got = torch.full_like(ref, float("nan"))
+            st = noalloc(options(L, N, dx0, precision, interp), rho, got)
+            assert st == m.NM_OK, m.last_error()
+            torch.cuda.synchronize()
+            a, b = got.cpu().numpy(), ref.cpu().numpy()
+            assert np.isfinite(a).all()
+            if precision == "fp64":
+                assert rel_max(a, b) <= FP64_REL_MAX
+            else:
+                assert rel_l2(a, b) <= FP32_REL_L2 and rel_max(a, b) <= FP32_REL_MAX
+
+
+@pytest.mark.parametrize("L,N,precision,interp", [
+    (2, 64, "fp64", "diagonal"), (2, 64, "fp32", "trilinear"), (15, 32, "fp64", "diagonal"),
+    (16, 32, "fp64", "trilinear"),
+])
+def test_rejects_meshes_beyond_the_static_maximum(L, N, precision, interp):
+    import torch
+    m = nm()
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    rho = torch.zeros((L, N, N, N), dtype=dt, device="cuda")
+    phi = torch.full((L, N, N, N), 7.0, dtype=torch.float64, device="cuda")
+    st = noalloc(options(L, N, 1.0 / N, precision, interp), rho, phi)
     assert st == m.NM_EINVAL
     assert "NM_NOALLOC_SCRATCH_BYTES" in m.last_error()
+    torch.cuda.synchronize()
+    assert bool((phi == 7.0).all())      # nothing was launched
