@@ -151,12 +151,23 @@ def reduce_2x(fine):
     return fine.reshape(n, 2, n, 2, n, 2).mean(axis=(1, 3, 5))
 
 
-def solve_components(rho, N, dx0, G=1.0, method="original", want=("full", "hole")):
+def _level_convolution(job):
+    """One level convolution of `solve_components` (a module-level function so
+    that a process pool can run it); the spectrum is built where it runs."""
+    M, dx, G = job
+    return isolated_convolution(M, dx, G)
+
+
+def solve_components(rho, N, dx0, G=1.0, method="original", want=("full", "hole"), mapper=None):
     """Per-level component potentials of the decomposition.
 
     Returns a dict with 'full' (Phi^m on Omega^m), 'hole' (Phi^m_hole on
     Omega^m_hole, None for the finest level), 'dbl' (reduced Phi^{m+1}_dbl on
     level m, pairwise-dipole method only) and 'rho' (restricted densities).
+
+    The level convolutions are independent of one another (Sect. 4); with
+    `mapper` (a map-like callable, e.g. a process pool's map) they are
+    evaluated through it, with the same arithmetic and the same results.
     """
     rho = np.asarray(rho, dtype=np.float64)
     L = rho.shape[0]
@@ -165,13 +176,20 @@ def solve_components(rho, N, dx0, G=1.0, method="original", want=("full", "hole"
         raise ValueError("rho must be (levels, N, N, N)")
     rho_r = restrict(rho, N)
     full_M, hole_M = level_masses(rho_r, geom)
-    spec = green_spectrum(N)
     out = {"rho": rho_r, "full": [None] * L, "hole": [None] * L, "dbl": [None] * L}
+    jobs = []
     for m in range(L):
         if "full" in want and (method == "original" or m == L - 1):
-            out["full"][m] = isolated_convolution(full_M[m], geom.dx(m), G, spec)
+            jobs.append(("full", m, full_M[m]))
         if hole_M[m] is not None:
-            out["hole"][m] = isolated_convolution(hole_M[m], geom.dx(m), G, spec)
+            jobs.append(("hole", m, hole_M[m]))
+    if mapper is None:
+        spec = green_spectrum(N)
+        res = [isolated_convolution(M, geom.dx(m), G, spec) for (_, m, M) in jobs]
+    else:
+        res = list(mapper(_level_convolution, [(M, geom.dx(m), G) for (_, m, M) in jobs]))
+    for (kind, m, _), r in zip(jobs, res):
+        out[kind][m] = r
     if method == "dipole":
         spec2 = green_spectrum(2 * N) if L > 1 else None
         for n in range(L - 1):
@@ -260,7 +278,7 @@ def triple_terms(rho_r, geom, G, quadrupled=True):
     return dbl, two
 
 
-def solve(rho, N, dx0, G=1.0, method="original", interp="diagonal"):
+def solve(rho, N, dx0, G=1.0, method="original", interp="diagonal", mapper=None):
     """Potential on every cell of every level, shape (levels, N, N, N).
 
     method='original' -- Eq. 14:
@@ -278,12 +296,12 @@ def solve(rho, N, dx0, G=1.0, method="original", interp="diagonal"):
         direct sum of Eq. B.6.
     interp='trilinear' takes each tilde Phi^k_hole straight from level k;
     interp='diagonal' replaces the sum over k < n by the carried term carry_n
-    (module docstring).
+    (module docstring).  `mapper`: see `solve_components`.
     """
     rho = np.asarray(rho, dtype=np.float64)
     L = rho.shape[0]
     triple = method in ("dipole3", "dipole3_ds")
-    comp = solve_components(rho, N, dx0, G, "dipole" if triple else method)
+    comp = solve_components(rho, N, dx0, G, "dipole" if triple else method, mapper=mapper)
     if triple:
         dbl3, two = triple_terms(comp["rho"], Geometry(L, N, dx0), G, quadrupled=method == "dipole3")
     if interp not in ("trilinear", "diagonal"):
