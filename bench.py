@@ -143,13 +143,17 @@ def pass_bytes(name, N, fp32):
     return None
 
 
+# the sources whose kernels the traffic summary measures
+HASHED_SOURCES = ("fft.cuh", "conv.cuh", "conv_inst.cuh", "conv_f32_pair.cu", "support.cu")
+
+
 def source_hash():
     """First 16 hex digits of the sha256 of the sources that define the
     measured passes' kernels, with comments and white space taken out (a
     comment edit leaves the kernels, and so their measured traffic, as they
     were)."""
     h = hashlib.sha256()
-    for f in ("fft.cuh", "conv.cuh", "conv_inst.cuh", "conv_f32_pair.cu", "support.cu"):
+    for f in HASHED_SOURCES:
         text = open(os.path.join(ROOT, "paper_2301_06763_gb300", "csrc", f)).read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)
@@ -224,7 +228,8 @@ def oracle_solve_timed(rho, N, dx0, pool=None):
 def cpu_baseline(levels, N):
     """The FP64 oracle, as it stands, on the host: one level convolution on one
     core (extrapolated to the 2L - 1 of a solve), and a whole solve with its
-    convolutions spread over all host cores."""
+    convolutions spread over all host cores.  Returns (the oracle's potential,
+    the timing record)."""
     import oracle
     from paper_2301_06763_gb300 import workloads as wl
     w = wl.config_contrast(levels=levels, N=N)
@@ -237,10 +242,10 @@ def cpu_baseline(levels, N):
     cores = min(os.cpu_count() or 1, nconv)
     pool = oracle_pool(cores)
     try:
-        _, t_all = oracle_solve_timed(rho, N, w.dx0, pool)
+        phi_oracle, t_all = oracle_solve_timed(rho, N, w.dx0, pool)
     finally:
         pool.shutdown()
-    return {"value": 1.0 / t_all, "unit": "solves/s", "cores": cores, "kind": "oracle",
+    return phi_oracle, {"value": 1.0 / t_all, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "host_cores": os.cpu_count(), "cpu": platform.processor() or platform.machine(),
             "sample": "one whole oracle solve (restriction, %d level convolutions spread over %d "
                       "processes, Eq. 14 assembly): %.1f s" % (nconv, cores, t_all),
@@ -249,43 +254,48 @@ def cpu_baseline(levels, N):
                                    "convolutions per solve" % (N, t, nconv)}}
 
 
-REF_SLAB = 8
-
-
 def reference_arm(args):
-    """--impl reference: the oracle on the host cores, bounded per step."""
+    """--impl reference: the FP64 oracle, as it stands, on the host cores.
+
+    One step = one whole oracle solve of the benchmark workload (restriction,
+    the 2L - 1 level convolutions spread over a spawn-started process pool on
+    the host cores, the Eq. 14 assembly with the carried Eqs. 3-6
+    interpolation), the same computation the GPU arm times, in FP64."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
+    from paper_2301_06763_gb300 import workloads as wl
     N, L = args.N, args.levels
-    P = 2 * N
-    rng = np.random.default_rng(0)
-    # one step = one oracle axis pass over REF_SLAB-th of the padded domain
-    # (P / REF_SLAB planes of lines), so that the default step counts end in
-    # a few minutes
-    x = rng.standard_normal((P // REF_SLAB, P, P)) + 1j * rng.standard_normal((P // REF_SLAB, P, P))
-    for _ in range(args.warmup):
-        oracle.fft_axis(x, -1)
-    t_all = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.fft_axis(x, -1)
-    total = time.perf_counter() - t_all
-    passes = 6 * (2 * L - 1)          # 3 forward + 3 inverse axis passes per convolution
-    per_step = total / args.steps
-    value = 1.0 / (passes * REF_SLAB * per_step)
+    w = wl.config_contrast(levels=L, N=N)
+    rho = w.rho()
+    nconv = 2 * L - 1
+    cores = min(os.cpu_count() or 1, nconv)
+    pool = oracle_pool(cores)
+    try:
+        for _ in range(args.warmup):
+            oracle_solve_timed(rho, N, w.dx0, pool)
+        times = []
+        for _ in range(args.steps):
+            times.append(oracle_solve_timed(rho, N, w.dx0, pool)[1])
+    finally:
+        pool.shutdown()
+    total = sum(times)
+    per_step = total / max(args.steps, 1)
+    value = args.steps / total if total > 0 else None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": per_step * 1e3, "p50_ms": pct(times, 50) * 1e3, "p99_ms": pct(times, 99) * 1e3,
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "contrast-%dx%d" % (L, N), "levels": L, "N": N,
-                   "precision": "fp64", "method": "original"},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "one oracle fft_axis pass over 1/%d of the (2N)^3 = %d^3 padded "
-                                   "domain per step; a solve is %d whole passes (%d convolutions"
-                                   " x 6) plus untimed pad/multiply/crop/assembly"
-                                   % (REF_SLAB, P, passes, 2 * L - 1)},
+                   "precision": "fp64 (the CPU oracle)", "method": "original",
+                   "interp": "diagonal (Eqs. 3-6, carried level by level)",
+                   "parallelism": "host processes"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "host_cores": os.cpu_count(), "cpu": platform.processor() or platform.machine(),
+                         "sample": "one whole oracle solve per step (restriction, %d level convolutions "
+                                   "spread over %d processes, Eq. 14 assembly)" % (nconv, cores)},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -463,6 +473,34 @@ def cufft_baseline(nm, torch, dev, rho, w, reps=10):
     return out
 
 
+def accuracy_vs_oracle(torch, p32, p64, rho32, rho64, phi_oracle, w):
+    """Errors of this solve on every cell: the FP32 mode and the FP64 path
+    against the oracle's potential (the one the cpu_baseline leg computed),
+    and all three against the closed-form potential of the density (Eq. 7's
+    measure, per level: max |Phi - Phi_exact| over max |Phi_exact| of all
+    levels)."""
+    from tests import analytic
+    got32 = p32.potential(rho32).cpu().numpy()
+    got64 = p64.potential(rho64).cpu().numpy()
+    torch.cuda.synchronize()
+    ref = phi_oracle
+    den = np.abs(ref).max()
+    an = [analytic.workload_potential(w, m) for m in range(w.levels)]
+    an_scale = max(np.abs(a).max() for a in an)
+
+    def per_level(x):
+        return [float(np.abs(x[m] - an[m]).max() / an_scale) for m in range(w.levels)]
+
+    return {"cells": "all %d" % ref.size, "reference": "FP64 oracle (the cpu_baseline solve)",
+            "fp32_rel_l2": float(np.linalg.norm(got32 - ref) / np.linalg.norm(ref)),
+            "fp32_rel_max": float(np.abs(got32 - ref).max() / den),
+            "fp64_rel_l2": float(np.linalg.norm(got64 - ref) / np.linalg.norm(ref)),
+            "fp64_rel_max": float(np.abs(got64 - ref).max() / den),
+            "tolerances": {"fp32_rel_l2": 2e-6, "fp32_rel_max": 1e-5, "fp64_rel_max": 1e-11},
+            "vs_closed_form_rel_max_per_level": {"oracle": per_level(ref), "fp32": per_level(got32),
+                                                 "fp64": per_level(got64)}}
+
+
 def max_over_ranks(torch, dist, v):
     from paper_2301_06763_gb300 import replicas
     return replicas.max_over_ranks(v, dist, device="cuda" if dist is not None else None)
@@ -591,8 +629,10 @@ def ours(args):
         cuf["speedup_fp32_passes"] = cuf["fp32_ms"] / cuf["ours_fp32_transform_passes_ms"]
         cuf["speedup_fp64_solve"] = cuf["fp64_ms"] / cuf["ours_fp64_solve_ms"]
     cpu = None
+    accuracy = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(L, N)
+        phi_oracle, cpu = cpu_baseline(L, N)
+        accuracy = accuracy_vs_oracle(torch, p32, p64, rho32[0], rho64[0], phi_oracle, w)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
@@ -623,6 +663,7 @@ def ours(args):
         "roofline": roof,
         "kernels": kernel_table,
         "cpu_baseline": cpu,
+        "accuracy": accuracy,
         "dipole": dip,
         "cufft_baseline": cuf,
         "acceleration": ext.get("acceleration"),

@@ -136,3 +136,60 @@ def poly_sphere_accel_radial(r, M, R, G=1.0):
     s = np.clip(r / R, 0.0, 1.0)
     m_in = 4.0 * math.pi * rho0 * R ** 3 * (s ** 3 / 3.0 - 2.0 * s ** 5 / 5.0 + s ** 7 / 7.0)
     return G * m_in / np.maximum(r, 1e-300) ** 2
+
+
+def box_integral_grid(px, py, pz, h):
+    """`box_integral` over the cube [-h, h]^3 at every point of the arrays
+    (px, py, pz): the same closed form, vectorised."""
+    px, py, pz = (np.asarray(v, dtype=float) for v in (px, py, pz))
+
+    def F(x, y, z):
+        R = np.sqrt(x * x + y * y + z * z)
+        v = np.zeros_like(R)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            v += np.where((x != 0) & (y != 0), x * y * np.log(z + R), 0.0)
+            v += np.where((y != 0) & (z != 0), y * z * np.log(x + R), 0.0)
+            v += np.where((z != 0) & (x != 0), z * x * np.log(y + R), 0.0)
+            v -= np.where(x != 0, 0.5 * x * x * np.arctan(y * z / (x * R)), 0.0)
+            v -= np.where(y != 0, 0.5 * y * y * np.arctan(z * x / (y * R)), 0.0)
+            v -= np.where(z != 0, 0.5 * z * z * np.arctan(x * y / (z * R)), 0.0)
+        return v
+
+    tot = np.zeros(np.broadcast(px, py, pz).shape)
+    for i, X in enumerate((-h - px, h - px)):
+        for j, Y in enumerate((-h - py, h - py)):
+            for k, Z in enumerate((-h - pz, h - pz)):
+                s = 1.0 if (i + j + k) % 2 == 1 else -1.0
+                tot = tot + s * F(X, Y, Z)
+    return tot
+
+
+def workload_potential(workload, level):
+    """The closed-form potential of a workload's density components at the
+    cell centres of `level` (shape (N, N, N), [z, y, x]): Plummer spheres and
+    homogeneous spheres by the shell theorem, a uniform background by the
+    prism formula over the coarsest cube (side N dx0, where the nested mesh
+    holds it).  Mass the mesh does not hold (a Plummer sphere's tail outside
+    the coarsest cube) is included, so the difference to a mesh solution
+    carries that truncation as well as the discretisation error."""
+    w = workload
+    N, dx = w.N, w.dx0 / 2.0 ** level
+    c = -N * dx / 2.0 + (np.arange(N) + 0.5) * dx
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    out = np.zeros((N, N, N))
+    for comp in w.components:
+        kind = type(comp).__name__
+        if kind in ("Plummer", "UniformSphere", "PolySphere"):
+            cx, cy, cz = comp.centre
+            r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+            if kind == "Plummer":
+                out += plummer(r, comp.mass, comp.scale, w.G)
+            elif kind == "UniformSphere":
+                out += uniform_sphere(r, comp.mass, comp.radius, w.G)
+            else:
+                out += poly_sphere(r, comp.mass, comp.radius, w.G)
+        elif kind == "Background":
+            out += -w.G * comp.value * box_integral_grid(x, y, z, 0.5 * N * w.dx0)
+        else:
+            raise ValueError("no closed form for %s" % kind)
+    return out

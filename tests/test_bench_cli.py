@@ -44,23 +44,25 @@ def test_oracle_solve_timed_matches_oracle():
 
 
 def test_traffic_summary_follows_the_kernel_sources(tmp_path, monkeypatch):
-    # the committed ncu summary matches the sources as they are; a comment or
-    # white-space edit keeps the hash, a code edit changes it and the lookup
-    # then reports no traffic
+    # a traffic summary stamped with the current source hash is read back; a
+    # comment or white-space edit keeps the hash, a code edit changes it and
+    # the lookup then reports no traffic
     import shutil
-    assert bench.ncu_traffic("zseam_f32_P256") is not None
-    base = bench.source_hash()
     csrc = tmp_path / "paper_2301_06763_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    for f in ("fft.cuh", "conv.cuh", "conv_inst.cuh", "conv_f32_pair.cu", "support.cu"):
+    for f in bench.HASHED_SOURCES:
         shutil.copy(os.path.join(ROOT, "paper_2301_06763_gb300", "csrc", f), csrc / f)
-    shutil.copytree(os.path.join(ROOT, "profiles"), tmp_path / "profiles")
+    (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.source_hash() == base
+    base = bench.source_hash()
+    (tmp_path / "profiles" / "ncu_traffic.md").write_text(
+        "source hash: `%s`\n\n| kernel | a | b | bytes per pair |\n|---|---|---|---|\n"
+        "| zseam_f32_P256 | x | y | 1.25e8 |\n" % base)
+    assert bench.ncu_traffic("zseam_f32_P256") == 1.25e8
     conv = csrc / "conv.cuh"
     conv.write_text("// a new comment\n" + conv.read_text().replace("namespace nm {", "namespace nm {\n\n/* block */ ", 1))
     assert bench.source_hash() == base
-    assert bench.ncu_traffic("zseam_f32_P256") is not None
+    assert bench.ncu_traffic("zseam_f32_P256") == 1.25e8
     conv.write_text(conv.read_text().replace("constexpr int kMaxPairs = 64;", "constexpr int kMaxPairs = 65;"))
     assert bench.source_hash() != base
     assert bench.ncu_traffic("zseam_f32_P256") is None

@@ -47,16 +47,6 @@ def test_fp32_full_size_sampled(contrast):
     assert np.max(np.abs(vals - ref)) <= FP32_REL_MAX * scale
 
 
-def test_fp32_against_fp64_everywhere_full_size(contrast):
-    # the mixed-precision tolerance over every cell, with the FP64 path
-    # (itself checked against the oracle above) as the reference
-    w, rho, sm, ref = contrast
-    a = gpu_solve(rho, w.N, w.dx0)
-    b = gpu_solve(rho.astype(np.float32), w.N, w.dx0, precision="fp32")
-    assert np.linalg.norm((a - b).ravel()) <= 2e-6 * np.linalg.norm(a.ravel())
-    assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(a))
-
-
 def test_linearity_full_size():
     w = wl.config_contrast()
     r1 = w.rho()

@@ -104,3 +104,14 @@ def test_spectrum_real_even_and_dct(N):
     Cm = np.cos(2 * np.pi * np.outer(k, j) / P) * w[None, :]
     dct = np.einsum("az,by,cx,zyx->abc", Cm, Cm, Cm, g)
     assert np.allclose(Sr[: N + 1, : N + 1, : N + 1], dct, rtol=0, atol=1e-11)
+
+
+def test_vectorised_box_formula_matches_the_scalar_one():
+    from tests.analytic import box_integral_grid
+    rng = np.random.default_rng(4)
+    pts = rng.uniform(-1.2, 1.2, (40, 3))
+    pts[0] = 0.0
+    pts[1] = (0.5, 0.0, 0.25)       # on a face
+    got = box_integral_grid(pts[:, 0], pts[:, 1], pts[:, 2], 0.5)
+    for p, g in zip(pts, got):
+        assert abs(g - box_integral(*p, -.5, .5, -.5, .5, -.5, .5)) < 1e-12 * max(1.0, abs(g))
