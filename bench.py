@@ -780,16 +780,24 @@ def serve_mode(args):
             reqs.append(Request(i, w.levels, w.N, w.dx0, dens[w.N][:w.levels], arrival=t,
                                 keep_result=False))
         srv = Server(budget, slots=4, precision="fp32")
-        # warm the pool: one request per shape, untimed
+        # plans, spectra and buffers for every shape of the request
+        # distribution, made before the stream starts (untimed), then one
+        # untimed request per shape so that each shape's solve graph exists
+        shapes = [(L, N) for N in (32, 64, 128, 256) for L in range(3, 11)]
+        srv.prewarm(shapes, per_shape=3)
+        made0 = srv.residents_made
         warm = [Request(-1 - i, L, N, 1.0 / N, dens[N][:L], keep_result=False)
                 for i, (L, N) in enumerate(sorted(set((r.levels, r.N) for r in reqs)))]
         run_stream(srv, warm)
         srv.completed.clear()
+        made1 = srv.residents_made
         elapsed, done = run_stream(srv, reqs)
         st = latency_stats(done)
         results.append({"rate": rate, "requests": count, "completed": len(done),
                         "failed": len(srv.failed), "solves_per_s": len(done) / elapsed,
-                        "batches": srv.batches, "peak_bytes": srv.peak_used, **st})
+                        "batches": srv.batches, "peak_bytes": srv.peak_used,
+                        "residents_prewarmed": made0, "residents_made_while_serving": srv.residents_made - made1,
+                        **st})
         srv.close()
         torch.cuda.empty_cache()
     print(json.dumps({"mode": "serve", "metric": "served solves/s and latency (arrival -> host potentials)",

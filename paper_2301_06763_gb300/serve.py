@@ -3,19 +3,22 @@
 Requests (one nested mesh each: levels, N, dx0, host density) arrive over
 time.  Every call to ``Server.step()``:
 
-1. retires the batches whose completion event has fired (their plans go back
-   to a pool of resident plans keyed by shape, their bytes back to the budget);
+1. retires the batches whose completion event has fired (each request's
+   resident set -- plan, device buffers and page-locked staging -- goes back
+   to a pool keyed by shape, its bytes back to the budget);
 2. admits waiting requests, oldest first, while a stream slot is free and the
    request's device footprint fits the HBM budget (``nm_footprint_bytes`` plus
-   its density and potential buffers; idle pooled plans are evicted, least
+   its density and potential buffers; idle resident sets are evicted, least
    recently used first, when the budget needs their memory);
 3. launches the admitted requests as one ``nm_batch_potential`` call on the
    free stream: upload of the densities, the batched solve and the download of
    the potentials, all ordered on that stream.
 
 Batches on different streams overlap on the device, and requests that arrive
-while earlier batches run join the next batch: continuous batching.  Plans and
-their Green spectra stay resident between requests of the same shape.  The
+while earlier batches run join the next batch: continuous batching.  Plans,
+their Green spectra and the request buffers stay resident between requests of
+the same shape (``Server.prewarm`` makes them ahead of the stream), so a
+request of a seen shape allocates neither device nor page-locked memory.  The
 arithmetic all runs in the CUDA library; this module only schedules.
 """
 import collections
@@ -47,6 +50,34 @@ class Request:
         return None if self.done is None else self.done - self.arrival
 
 
+class _Resident:
+    """What one request shape keeps on the device between requests: a plan
+    (its workspace and Green spectrum) and the density and potential buffers,
+    with page-locked host staging for both, so that serving a request of a
+    seen shape allocates nothing."""
+
+    def __init__(self, torch, key, precision, interp, device):
+        L, N, dx0, G, method = key
+        self.key = key
+        self.plan = nm.Plan(L, N, dx0, G, precision=precision, method=method, interp=interp)
+        shape = (L, N, N, N)
+        dt = torch.float32 if precision == "fp32" else torch.float64
+        try:
+            self.rho_dev = torch.empty(shape, dtype=dt, device=device)
+            self.phi_dev = torch.empty(shape, dtype=torch.float64, device=device)
+            self.rho_pin = torch.empty(shape, dtype=dt, pin_memory=True)
+            self.phi_pin = torch.empty(shape, dtype=torch.float64, pin_memory=True)
+        except Exception:
+            self.plan.close()
+            raise
+        self.bytes = self.plan.workspace_bytes() + self.rho_dev.nbytes + self.phi_dev.nbytes
+
+    def close(self):
+        if self.plan is not None:
+            self.plan.close()
+        self.plan = self.rho_dev = self.phi_dev = self.rho_pin = self.phi_pin = None
+
+
 class Server:
     def __init__(self, hbm_budget_bytes, slots=4, precision="fp32", max_batch=64, device=None, interp="diagonal"):
         import torch
@@ -60,45 +91,86 @@ class Server:
         self.max_batch = int(max_batch)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         self.free = list(range(slots))
-        self.pool = collections.OrderedDict()   # (L, N, dx0, G, method) -> [Plan], LRU order
+        self.pool = collections.OrderedDict()   # key -> [_Resident], least recently used first
         self.pool_bytes = 0
         self.queue = collections.deque()
         self.inflight = []
         self.completed = []
         self.failed = []
         self.batches = 0
+        self.residents_made = 0
 
     # ------------------------------------------------------------------ memory
     def _dtype(self):
         return self.torch.float32 if self.precision == "fp32" else self.torch.float64
 
+    @staticmethod
+    def _key(r):
+        return (r.levels, r.N, r.dx0, r.G, r.method)
+
     def request_bytes(self, r, with_plan=True):
+        """Device bytes a request of this shape occupies: its density and
+        potential buffers, and (with_plan) the plan's workspace."""
         cells = r.levels * r.N ** 3
         b = cells * (_ES[self.precision] + 8)
         if with_plan:
             b += nm.footprint_bytes(r.levels, r.N, r.dx0, r.G, self.precision, r.method, self.interp)
         return b
 
-    def _take_plan(self, r):
-        key = (r.levels, r.N, r.dx0, r.G, r.method)
-        plans = self.pool.get(key)
-        if plans:
-            p = plans.pop()
-            self.pool_bytes -= p.workspace_bytes()
-            if not plans:
-                del self.pool[key]
-            return p, False
-        return None, True
+    def _pool_put(self, res):
+        self.pool.setdefault(res.key, []).append(res)
+        self.pool.move_to_end(res.key)
+        self.pool_bytes += res.bytes
+
+    def _pool_take(self, key):
+        lst = self.pool.get(key)
+        if not lst:
+            return None
+        res = lst.pop()
+        self.pool_bytes -= res.bytes
+        if not lst:
+            del self.pool[key]
+        return res
 
     def _evict_until(self, need):
         while self.used + self.pool_bytes + need > self.budget and self.pool:
-            key, plans = next(iter(self.pool.items()))
-            p = plans.pop()
-            self.pool_bytes -= p.workspace_bytes()
-            p.close()
-            if not plans:
+            key, lst = next(iter(self.pool.items()))
+            res = lst.pop()
+            self.pool_bytes -= res.bytes
+            res.close()
+            if not lst:
                 del self.pool[key]
         return self.used + self.pool_bytes + need <= self.budget
+
+    def _make(self, key):
+        res = _Resident(self.torch, key, self.precision, self.interp, self.device)
+        self.residents_made += 1
+        return res
+
+    def prewarm(self, shapes, per_shape=1, method="original", G=1.0):
+        """Make plans, Green spectra and buffers for request shapes ahead of
+        time: ``shapes`` = iterable of (levels, N) (dx0 = 1/N) or (levels, N,
+        dx0); ``per_shape`` residents each, while the HBM budget allows (the
+        smallest shapes first).  Returns the number made."""
+        made = 0
+        keys = []
+        for sh in shapes:
+            L, N = int(sh[0]), int(sh[1])
+            dx0 = float(sh[2]) if len(sh) > 2 else 1.0 / N
+            keys.append((L, N, dx0, float(G), method))
+        keys.sort(key=lambda k: k[0] * k[1] ** 3)
+        for key in keys:
+            for _ in range(per_shape - len(self.pool.get(key, []))):
+                need = nm.footprint_bytes(key[0], key[1], key[2], key[3], self.precision, key[4], self.interp) \
+                    + key[0] * key[1] ** 3 * (_ES[self.precision] + 8)
+                if self.used + self.pool_bytes + need > self.budget:
+                    return made
+                res = self._make(key)
+                res.plan.green()
+                self._pool_put(res)
+                made += 1
+        self.torch.cuda.synchronize(self.device)
+        return made
 
     # ------------------------------------------------------------------ loop
     def submit(self, r):
@@ -112,13 +184,10 @@ class Server:
                 for r in batch:
                     r.done = now
                     if r.keep_result:
-                        r.result = r._phi_host.numpy()
+                        r.result = r._res.phi_pin.numpy().copy()
                     self.used -= r.bytes
-                    key = (r.levels, r.N, r.dx0, r.G, r.method)
-                    self.pool.setdefault(key, []).append(r._plan)
-                    self.pool.move_to_end(key)
-                    self.pool_bytes += r._plan.workspace_bytes()
-                    r._plan = r._rho_dev = r._phi_dev = r._rho_pin = r._phi_host = None
+                    self._pool_put(r._res)
+                    r._res = None
                     self.completed.append(r)
                 self.free.append(si)
             else:
@@ -129,11 +198,10 @@ class Server:
         batch = []
         while self.queue and len(batch) < self.max_batch:
             r = self.queue[0]
-            plan, need_plan = self._take_plan(r)
+            key = self._key(r)
+            res = self._pool_take(key)
             try:
-                need = self.request_bytes(r, with_plan=need_plan)
-                if plan is not None:        # a pooled plan's workspace moves from the pool to `used`
-                    need += plan.workspace_bytes()
+                need = res.bytes if res is not None else self.request_bytes(r)
             except Exception as e:          # invalid shape: rejected by the library
                 self.queue.popleft()
                 r.error = str(e)
@@ -142,27 +210,24 @@ class Server:
             if need > self.budget:
                 self.queue.popleft()
                 r.error = "footprint %d bytes exceeds the HBM budget %d" % (need, self.budget)
-                if plan is not None:
-                    self.pool.setdefault((r.levels, r.N, r.dx0, r.G, r.method), []).append(plan)
-                    self.pool_bytes += plan.workspace_bytes()
+                if res is not None:
+                    self._pool_put(res)
                 self.failed.append(r)
                 continue
             if not self._evict_until(need):
-                if plan is not None:
-                    self.pool.setdefault((r.levels, r.N, r.dx0, r.G, r.method), []).append(plan)
-                    self.pool_bytes += plan.workspace_bytes()
+                if res is not None:
+                    self._pool_put(res)
                 break
             self.queue.popleft()
-            try:
-                if plan is None:
-                    plan = nm.Plan(r.levels, r.N, r.dx0, r.G, precision=self.precision, method=r.method,
-                                   interp=self.interp)
-                    need = self.request_bytes(r, with_plan=False) + plan.workspace_bytes()
-            except Exception as e:          # invalid shape or allocation failure
-                r.error = str(e)
-                self.failed.append(r)
-                continue
-            r._plan = plan
+            if res is None:
+                try:
+                    res = self._make(key)
+                except Exception as e:      # invalid shape or allocation failure
+                    r.error = str(e)
+                    self.failed.append(r)
+                    continue
+                need = res.bytes
+            r._res = res
             r.bytes = need
             self.used += need
             self.peak_used = max(self.peak_used, self.used + self.pool_bytes)
@@ -183,21 +248,20 @@ class Server:
         s = self.streams[si]
         with torch.cuda.stream(s):
             for r in batch:
-                shape = (r.levels, r.N, r.N, r.N)
-                if isinstance(r.rho, torch.Tensor) and r.rho.is_pinned() and r.rho.dtype == self._dtype():
-                    r._rho_pin = r.rho                  # caller-pinned: no host copy
+                res = r._res
+                rho = r.rho
+                if isinstance(rho, torch.Tensor) and rho.is_pinned() and rho.dtype == self._dtype() \
+                        and rho.is_contiguous():
+                    src = rho                       # caller-pinned: straight from there
                 else:
-                    arr = r.rho.numpy() if isinstance(r.rho, torch.Tensor) else r.rho
-                    r._rho_pin = torch.from_numpy(np.ascontiguousarray(
-                        arr, dtype=np.float32 if self.precision == "fp32" else np.float64)).pin_memory()
-                r._rho_dev = torch.empty(shape, dtype=self._dtype(), device=self.device)
-                r._phi_dev = torch.empty(shape, dtype=torch.float64, device=self.device)
-                r._rho_dev.copy_(r._rho_pin, non_blocking=True)
-            nm.batch_potential([r._plan for r in batch], [r._rho_dev for r in batch],
-                               [r._phi_dev for r in batch], stream=s)
+                    arr = rho.numpy() if isinstance(rho, torch.Tensor) else np.asarray(rho)
+                    np.copyto(res.rho_pin.numpy(), arr, casting="same_kind")
+                    src = res.rho_pin
+                res.rho_dev.copy_(src, non_blocking=True)
+            nm.batch_potential([r._res.plan for r in batch], [r._res.rho_dev for r in batch],
+                               [r._res.phi_dev for r in batch], stream=s)
             for r in batch:
-                r._phi_host = torch.empty(r._phi_dev.shape, dtype=torch.float64, pin_memory=True)
-                r._phi_host.copy_(r._phi_dev, non_blocking=True)
+                r._res.phi_pin.copy_(r._res.phi_dev, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
         self.inflight.append((si, ev, batch))
@@ -214,9 +278,9 @@ class Server:
 
     def close(self):
         self.drain()
-        for plans in self.pool.values():
-            for p in plans:
-                p.close()
+        for lst in self.pool.values():
+            for res in lst:
+                res.close()
         self.pool.clear()
         self.pool_bytes = 0
 

@@ -91,3 +91,22 @@ def test_mixed_methods_alone_and_in_the_mix():
             ref = p.potential(torch.from_numpy(r.rho).cuda()).cpu().numpy()
         assert np.array_equal(r.result, ref), r.method
     srv.close()
+
+
+def test_prewarmed_shapes_allocate_nothing_while_serving():
+    # with the request shapes prewarmed, the request loop makes no plan and no
+    # buffer (no cudaMalloc, no page-locked allocation) and every result
+    # still equals the request solved alone
+    from paper_2301_06763_gb300.serve import Server, run_stream
+    nm()
+    reqs = requests(20, seed=4, spacing=0.001)
+    shapes = sorted(set((r.levels, r.N) for r in reqs))
+    srv = Server(hbm_budget_bytes=2 << 30, slots=2, precision="fp32", max_batch=1)
+    made = srv.prewarm(shapes, per_shape=2)
+    assert made == 2 * len(shapes)
+    run_stream(srv, reqs)
+    assert len(srv.completed) == 20 and not srv.failed
+    assert srv.residents_made == made
+    for r in reqs:
+        assert np.array_equal(r.result, solo(r))
+    srv.close()
