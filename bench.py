@@ -722,6 +722,21 @@ def batch_mode(args):
     per_batch_launches = nm.kernel_launches() - l0
     ms_batch = timed(lambda: nm.batch_potential(plans32, r32, phis), args.steps)
     ms_seq32 = timed(lambda: [p.potential(r, f) for p, r, f in zip(plans32, r32, phis)], args.steps)
+    # the persistent schedule: every step of all 64 solves as work items of
+    # one launch (after a first eager call, replayed as a graph of one counter
+    # reset and one kernel)
+    keep = [p.schedule() for p in plans32]
+    for p in plans32:
+        p.set_schedule(p.levels, 16, 0, 0, 3)
+    nm.batch_potential(plans32, r32, phis)
+    torch.cuda.synchronize()
+    l0 = nm.kernel_launches()
+    nm.batch_potential(plans32, r32, phis)
+    torch.cuda.synchronize()
+    persist_launches = nm.kernel_launches() - l0
+    ms_persist = timed(lambda: nm.batch_potential(plans32, r32, phis), args.steps)
+    for p, sc in zip(plans32, keep):
+        p.set_schedule(**sc)
     ms_seq64 = timed(lambda: [p.potential(r, f) for p, r, f in zip(plans64, r64, phis)],
                      max(1, args.steps // 4))
     line = {"mode": "batch", "metric": "meshes/s, 64-mesh batch (N in {32,64,128}, 2-8 levels)",
@@ -729,6 +744,9 @@ def batch_mode(args):
             "fp32_one_by_one_ms": ms_seq32, "fp64_plain_one_by_one_ms": ms_seq64,
             "speedup_vs_fp64_plain": ms_seq64 / ms_batch, "speedup_vs_fp32_one_by_one": ms_seq32 / ms_batch,
             "cells": cells, "kernels_per_batch_eager": per_batch_launches,
+            "persistent": {"ms_per_batch": ms_persist, "meshes_per_s": 64 / (ms_persist / 1e3),
+                           "kernels_per_batch": persist_launches,
+                           "what": "all 64 solves as work items of one persistent launch (fuse 3)"},
             "graph": "batch replayed as one CUDA graph after the first repeat",
             "shapes": sorted(set((w.levels, w.N) for w in meshes)),
             "schedules": {"%dx%d" % k: v for k, v in tuned.items()}, "steps": args.steps,

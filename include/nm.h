@@ -231,14 +231,23 @@ typedef struct {
                     working set in L2 for the next pass                      */
     int radix;   /* values per thread = first-pass radix: 16 or 8             */
     int tile;    /* column tile of the strided passes: 0 = 128-byte rows,
-                    1 = 256-byte rows                                         */
+                    1 = 256-byte rows; with fuse 2, the CTAs per kx plane:
+                    0 = the default split for P, 1 = the alternative one
+                    (P = 128: 4 instead of 2; P = 256: 2 instead of 4)        */
     int pipeline;/* z-seam pass: 0 = one tile per CTA; 1 = persistent CTAs fed
                     by a two-stage TMA (cp.async.bulk.tensor) pipeline;
                     2 = two columns per thread on paired FP32 instructions
                     (FP32 plans, radix 16, P = 2N >= 64, fuse 0)              */
     int fuse;    /* 1 = x and y passes fused per z-slab through a thread-block
                     cluster (distributed shared memory), 3 launches per level
-                    group instead of 5; needs radix 16; 0 = five passes       */
+                    group instead of 5; needs radix 16; 0 = five passes;
+                    2 = three passes: x-forward writing kx-major planes, one
+                    pass per kx plane doing the y, z, spectrum multiply,
+                    inverse z and inverse y steps in shared memory (the ky
+                    residues split over a thread-block cluster whose partial
+                    sums meet in distributed shared memory), x-inverse
+                    (FP32 plans of the original method, radix 16, pipeline
+                    0, P = 2N in 64 .. 512)                                   */
 } nm_schedule;
 
 /* Read / set the schedule (set reallocates the work buffers when group
@@ -247,7 +256,7 @@ nm_status nm_get_schedule(nm_plan_t plan, nm_schedule* out);
 nm_status nm_set_schedule(nm_plan_t plan, const nm_schedule* sched);
 
 /* Autotuner: times every candidate schedule (group in {1, 2, all}, radix in
- * {16, 8}, tile in {0, 1}, pipeline in {0, 1, 2}, fuse in {0, 1}, where valid) with CUDA events over `reps` solves of the
+ * {16, 8}, tile in {0, 1}, pipeline in {0, 1, 2}, fuse in {0, 1, 2}, where valid) with CUDA events over `reps` solves of the
  * caller's rho into phi (phi is overwritten), on `stream`, keeps the fastest
  * on the plan and records it in a process-wide table keyed by (device name,
  * N, levels, precision, method) that later plans of the same key start from.

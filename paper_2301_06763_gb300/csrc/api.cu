@@ -98,6 +98,7 @@ struct Spectrum {
     float* d32 = nullptr;
     df* ddf = nullptr;
     float* d32x = nullptr;   // float rows over all kx (paired FP32 z-seam), on demand
+    float* d32z = nullptr;   // float octant with fz fastest (three-pass form), on demand
 };
 struct Twiddle {
     int dev = -1, P = 0;
@@ -168,6 +169,7 @@ static void release_spectrum(Spectrum* s) {
     cudaFree(s->d32);
     cudaFree(s->ddf);
     cudaFree(s->d32x);
+    cudaFree(s->d32z);
     for (size_t i = 0; i < g_spectra.size(); ++i)
         if (g_spectra[i] == s) { g_spectra.erase(g_spectra.begin() + i); break; }
     delete s;
@@ -228,6 +230,30 @@ const float* unfolded_spectrum(const float* spec) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     for (Spectrum* s : g_spectra)
         if (s->d32 == spec) return s->d32x;
+    return nullptr;
+}
+
+// The float octant with fz fastest that the three-pass form's fused y/z/y
+// pass reads (built once per spectrum, after the octant; synchronous).
+static nm_status build_zfast(Spectrum* s, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (s->d32z) return NM_OK;
+    float* out = nullptr;
+    cudaError_t e = cudaMalloc(&out, octant_count(s->N) * sizeof(float));
+    if (e == cudaSuccess) e = run_zfast(s->d64, out, s->N, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaFree(out);
+        return cuda_fail(e, "z-fast spectrum");
+    }
+    s->d32z = out;
+    return NM_OK;
+}
+
+const float* zfast_spectrum(const float* spec) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (Spectrum* s : g_spectra)
+        if (s->d32 == spec) return s->d32z;
     return nullptr;
 }
 
@@ -497,8 +523,22 @@ bool sched_valid(nm_plan_t p, const nm_schedule& sc) {
     if (sc.pipeline < 0 || sc.pipeline > 2) return false;
     // two columns per thread: FP32 level grids, 16 values per thread, P >= 64
     if (sc.pipeline == 2 && (!p->fp32 || p->dfx || sc.radix != 16 || p->P < 64 || sc.fuse)) return false;
-    if (sc.fuse != 0 && sc.fuse != 1) return false;
+    if (sc.fuse < 0 || sc.fuse > 3) return false;
     if (sc.fuse && sc.radix != 16) return false;
+    // three-pass form (fused y/z/y per kx plane): FP32 level grids of the
+    // original method, 2N in 64 .. 512; tile picks the CTAs per plane (1: the
+    // alternative split, built for 2N = 128 and 256); the z-seam choice does
+    // not apply
+    if (sc.fuse == 2) {
+        if (!p->fp32 || p->dfx || p->dipole || p->P < 64 || p->P > 512 || sc.pipeline != 0) return false;
+        if (sc.tile == 1 && p->P != 128 && p->P != 256) return false;
+    }
+    // persistent form: every step of the solve (and of every mesh batched
+    // with it) as work items of one launch; FP32 original method, 2N in
+    // 64 .. 512, the one-column z-seam and plain tiles
+    if (sc.fuse == 3 && (!p->fp32 || p->dfx || p->dipole || p->P < 64 || p->P > 512 || sc.pipeline != 0 ||
+                         sc.tile != 0))
+        return false;
     return sc.tile == 0 || sc.tile == 1;
 }
 
@@ -513,7 +553,35 @@ std::mutex g_graph_mu;
 std::vector<BatchGraph> g_graphs;   // most recent last
 constexpr size_t kMaxGraphs = 32;
 
+// Laid-out persistent batches (their device tables), keyed like the graphs;
+// a captured graph may reference one, so an entry lives until a plan of it
+// is destroyed or rescheduled, or until the cache is full (then every graph
+// goes too).
+struct PersistEntry {
+    std::vector<const void*> key;
+    PersistBatch* b;
+};
+std::mutex g_persist_mu;
+std::vector<PersistEntry> g_persist;   // most recent last
+constexpr size_t kMaxPersist = 256;
+
+void persist_drop_plan(nm_plan_t p) {
+    std::lock_guard<std::mutex> lk(g_persist_mu);
+    for (size_t i = 0; i < g_persist.size();) {
+        bool uses = false;
+        for (const void* k : g_persist[i].key)
+            if (k == (const void*)p) uses = true;
+        if (uses) {
+            persist_free(g_persist[i].b);
+            g_persist.erase(g_persist.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
 void graphs_drop_plan(nm_plan_t p) {
+    persist_drop_plan(p);
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (size_t i = 0; i < g_graphs.size();) {
         bool uses = false;
@@ -844,9 +912,15 @@ cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, int geom, const nm_
             if constexpr (sizeof(T) == 4) return run_conv_qdp_f32(pairs, n, P, spec, tw, s);
             else return run_conv_qdp_f64(pairs, n, P, spec, tw, s);
         }
+        if constexpr (sizeof(T) == 4) {
+            // three-pass form where the pairs allow it (a level's full and
+            // hole fields on aligned buffers), else the five passes
+            if (geom == 0 && sc.fuse == 2 && yzy_pairs_ok(pairs, n))
+                return run_conv_f32_yzy(pairs, n, P, sc.tile, spec, tw, s);
+        }
         const bool e16 = dbl || (sc.radix == 16 && P >= 16);
-        const int flags = (sc.tile ? CONV_WIDE : 0) | (sc.pipeline == 1 ? CONV_TMA : 0) |
-                          (sc.pipeline == 2 ? CONV_PAIRED : 0) | (sc.fuse ? CONV_FUSED : 0);
+        const int flags = (sc.fuse != 2 && sc.tile ? CONV_WIDE : 0) | (sc.pipeline == 1 ? CONV_TMA : 0) |
+                          (sc.pipeline == 2 ? CONV_PAIRED : 0) | (sc.fuse == 1 ? CONV_FUSED : 0);
         if constexpr (sizeof(T) == 4) {
             return e16 ? run_conv_f32_e16(pairs, n, P, dbl, flags, spec, tw, s)
                        : run_conv_f32_e8(pairs, n, P, dbl, flags, spec, tw, s);
@@ -872,7 +946,7 @@ nm_status enqueue_restrict(nm_plan_t p, const void* rho, cudaStream_t s) {
 }
 
 template <typename T>
-nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
+AssembleArgs<T> assemble_args(nm_plan_t p, double* phi) {
     const int L = p->L, N = p->N;
     const size_t N3 = (size_t)N * N * N;
     const size_t nc = N / 2 + 2, nc3 = nc * nc * nc;
@@ -881,6 +955,9 @@ nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
     a.phi = phi;
     a.levels = L;
     a.N = N;
+    // the carried Eqs. 3-6 rule reads level n-1 only (the hole crop, or the
+    // carried sum once the carry chain has run); trilinear reads every k < n
+    a.diag = p->opt.interp == NM_INTERP_DIAGONAL ? 1 : 0;
     for (int n = 0; n < L; ++n) {
         a.base[n] = lvl + (size_t)n * N3;
         a.dbl[n] = (p->dipole && n < L - 1) ? (const T*)p->dbl_out + (size_t)n * 8 * N3 : nullptr;
@@ -897,7 +974,12 @@ nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
             }
         }
     }
-    cudaError_t e = run_assemble_interp<T>(a, p->opt.interp, (T*)p->carry, s);
+    return a;
+}
+
+template <typename T>
+nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
+    cudaError_t e = run_assemble_interp<T>(assemble_args<T>(p, phi), p->opt.interp, (T*)p->carry, s);
     if (e != cudaSuccess) return cuda_fail(e, "assembly");
     return NM_OK;
 }
@@ -909,12 +991,124 @@ struct Item {
     double* phi;
 };
 
+// The solves of plans with the persistent schedule (fuse 3): one laid-out
+// batch per set of (plan, rho, phi), built on first use (synchronously, so
+// not while the caller captures a graph), then one counter reset and one
+// launch per call.
+std::vector<const void*> items_key(const std::vector<Item>& items) {
+    std::vector<const void*> key;
+    for (const Item& it : items) {
+        key.push_back(it.p);
+        key.push_back(it.rho);
+        key.push_back(it.phi);
+        const nm_schedule& sc = it.p->sched;
+        key.push_back((const void*)(uintptr_t)((sc.group << 12) | (sc.radix << 4) | (sc.fuse << 3) |
+                                               (sc.tile << 2) | sc.pipeline));
+    }
+    return key;
+}
+
+void graphs_drop_all() {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto& g : g_graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    g_graphs.clear();
+}
+
+nm_status enqueue_persistent(const std::vector<Item>& items, cudaStream_t s) {
+    const std::vector<const void*> key = items_key(items);
+    PersistBatch* b = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_persist_mu);
+        for (size_t i = 0; i < g_persist.size(); ++i)
+            if (g_persist[i].key == key) {
+                PersistEntry e = g_persist[i];
+                g_persist.erase(g_persist.begin() + i);
+                g_persist.push_back(e);
+                b = e.b;
+                break;
+            }
+    }
+    if (!b) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+            return fail(NM_EUNSUPPORTED, "persistent schedule: make one call with these buffers before capturing it");
+        std::vector<PersistMesh> meshes;
+        for (const Item& it : items) {
+            nm_plan_t p = it.p;
+            PersistMesh m;
+            m.P = p->P;
+            m.L = p->L;
+            m.group = p->sched.group;
+            m.rho = (const float*)it.rho;
+            m.restr = (float*)p->restr;
+            m.phi = it.phi;
+            m.work = p->work;
+            m.spec = spec_of<float>(p->spec);
+            m.tw = tw_of<float>(p->tw);
+            level_pairs<float>(p, it.rho, m.pairs);
+            m.carry = (p->opt.interp == NM_INTERP_DIAGONAL && p->L > 2) ? (float*)p->carry : nullptr;
+            m.asm_args = assemble_args<float>(p, it.phi);
+            meshes.push_back(std::move(m));
+        }
+        b = persist_new();
+        if (!b) return fail(NM_ENOMEM, "host allocation");
+        if (!persist_layout(meshes, *b)) {
+            persist_free(b);
+            return fail(NM_EUNSUPPORTED, "persistent schedule: a mesh of this batch does not fit it (buffers must "
+                                         "be 16-byte aligned)");
+        }
+        cudaError_t e = persist_upload(*b);
+        if (e != cudaSuccess) {
+            persist_free(b);
+            return cuda_fail(e, "persistent batch tables");
+        }
+        bool drop_graphs = false;
+        {
+            std::lock_guard<std::mutex> lk(g_persist_mu);
+            if (g_persist.size() >= kMaxPersist) {
+                // a graph may still reference the oldest tables: wait for the
+                // device, drop every graph, then free them
+                drop_graphs = true;
+                cudaDeviceSynchronize();
+                persist_free(g_persist.front().b);
+                g_persist.erase(g_persist.begin());
+            }
+            g_persist.push_back(PersistEntry{key, b});
+        }
+        if (drop_graphs) graphs_drop_all();
+    }
+    cudaError_t e = persist_launch(*b, s);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent batch");
+    return NM_OK;
+}
+
 // Restriction, level and doubled-grid convolutions round by round, assembly.
 // Every mesh uses its own workspace; in round r mesh i contributes pairs
 // [r g_i, (r+1) g_i) and contributions with equal (P, radix, tile) share a
-// launch per pass.
+// launch per pass.  Plans with the persistent schedule go to one persistent
+// launch instead.
+template <typename T>
+nm_status enqueue_items_rounds(const std::vector<Item>& items, cudaStream_t s);
+
 template <typename T>
 nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4 && !is_df<T>::value) {
+        std::vector<Item> pers, rest;
+        for (const Item& it : items) (it.p->sched.fuse == 3 ? pers : rest).push_back(it);
+        if (!pers.empty()) {
+            nm_status st = enqueue_persistent(pers, s);
+            if (st != NM_OK) return st;
+        }
+        if (rest.empty()) return NM_OK;
+        return enqueue_items_rounds<T>(rest, s);
+    } else {
+        return enqueue_items_rounds<T>(items, s);
+    }
+}
+
+template <typename T>
+nm_status enqueue_items_rounds(const std::vector<Item>& items, cudaStream_t s) {
     nm_status st;
     for (const Item& it : items)
         if ((st = enqueue_restrict<T>(it.p, it.rho, s)) != NM_OK) return st;
@@ -1007,7 +1201,11 @@ nm_status ensure_green(nm_plan_t p, cudaStream_t s) {
         nm_status st = nm_green(p, (void*)s);
         if (st != NM_OK) return st;
     }
-    if (p->sched.pipeline == 2 && !p->spec->d32x) return build_unfolded(p->spec, s);
+    if (p->sched.pipeline == 2 && !p->spec->d32x) {
+        nm_status st = build_unfolded(p->spec, s);
+        if (st != NM_OK) return st;
+    }
+    if (p->sched.fuse == 2 && !p->spec->d32z) return build_zfast(p->spec, s);
     return NM_OK;
 }
 
@@ -1051,15 +1249,7 @@ nm_status time_solves(nm_plan_t p, const void* rho, double* phi, int reps, cudaS
 // (captured on its first repeat); a new set runs eagerly.  Graphs bake in the
 // pointers and schedules, which form the key.
 nm_status run_items(const std::vector<Item>& items, cudaStream_t s) {
-    std::vector<const void*> key;
-    for (const Item& it : items) {
-        key.push_back(it.p);
-        key.push_back(it.rho);
-        key.push_back(it.phi);
-        const nm_schedule& sc = it.p->sched;
-        key.push_back((const void*)(uintptr_t)((sc.group << 12) | (sc.radix << 4) | (sc.fuse << 3) |
-                                               (sc.tile << 2) | sc.pipeline));
-    }
+    const std::vector<const void*> key = items_key(items);
     for (const Item& it : items) {
         nm_status st = ensure_green(it.p, s);
         if (st != NM_OK) return st;
@@ -1230,7 +1420,9 @@ nm_status nm_set_schedule(nm_plan_t p, const nm_schedule* sc) {
     if (!sched_valid(p, *sc))
         return fail(NM_EINVAL,
                     "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile 0 or 1, pipeline 0, 1 "
-                    "or 2 (2: FP32, radix 16, P >= 64, not fused)",
+                    "or 2 (2: FP32, radix 16, P >= 64, not fused), fuse 0, 1 or 2 (2: FP32 original method, "
+                    "radix 16, pipeline 0, 64 <= P <= 512, tile 1 only for P = 128 or 256) or 3 (FP32 original method, "
+                    "radix 16, pipeline 0, tile 0, 64 <= P <= 512)",
                     p->npairs);
     nm_status st = ensure_work_slots(p, sc->group);
     if (st != NM_OK) return st;
@@ -1250,7 +1442,7 @@ nm_status nm_autotune(nm_plan_t p, const void* rho, double* phi, int reps, void*
         for (int radix : {16, 8})
             for (int tile : {0, 1})
                 for (int pipe : {2, 1, 0})
-                    for (int fuse : {1, 0}) {
+                    for (int fuse : {3, 2, 1, 0}) {
                         nm_schedule c{g, radix, tile, pipe, fuse};
                         if (!sched_valid(p, c)) continue;
                         bool dup = false;
@@ -1318,8 +1510,10 @@ nm_status nm_spectrum_bytes(nm_plan_t p, size_t* bytes) {
     size_t b = octant_count(p->N) * per;
     if (p->spec_dbl) b += octant_count(2 * p->N) * per;
     if (p->spec_qdp) b += octant_count(4 * p->N) * per;
-    // float rows over all kx, for the paired FP32 z-seam (P >= 64)
+    // float rows over all kx, for the paired FP32 z-seam (P >= 64), and the
+    // float octant with fz fastest, for the three-pass form
     if (p->fp32 && p->P >= 64) b += (size_t)(p->N + 1) * (p->N + 1) * p->P * sizeof(float);
+    if (p->fp32 && p->P >= 64) b += octant_count(p->N) * sizeof(float);
     *bytes = b;
     return NM_OK;
 }

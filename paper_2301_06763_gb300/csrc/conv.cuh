@@ -127,18 +127,21 @@ template <int P, int E, int GM> struct Geo {
 };
 
 // ---------------------------------------------------------------- pass 1
+// The body of each pass is a device function of (pair, tile, shared memory)
+// that its kernel calls with its block indices, and that the persistent
+// batch kernel (persist.cu) calls for the work items it takes; 256 threads
+// for the row passes, TX P / E for the column passes.
 template <typename T, typename TIN, int P, int E, int GM>
-__global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T> a) {
+__device__ __forceinline__ void xfwd_body(const PairDesc<T>& d, const cpx<T>* tw, unsigned tile,
+                                          unsigned char* smem_raw) {
     using G = Geo<P, E, GM>;
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
-    const PairDesc<T>& d = a.pair[blockIdx.y];
-    load_twiddles<P, E, true>(sm_tw, a.tw);
+    load_twiddles<P, E, true>(sm_tw, tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
-    const int row0 = blockIdx.x * LINES;
+    const int row0 = tile * LINES;
     const int row = row0 + line;
     const bool valid = row < G::NIN * G::NIN;
     const int zi = row / G::NIN, yi = row % G::NIN;
@@ -198,6 +201,12 @@ __global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T
 #pragma unroll
         for (int s = 0; s < E; ++s) dst[out_index<P, E>(j, s)] = v[s];
     }
+}
+
+template <typename T, typename TIN, int P, int E, int GM>
+__global__ void __launch_bounds__(256) k_xfwd(const __grid_constant__ ConvArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xfwd_body<T, TIN, P, E, GM>(a.pair[blockIdx.y], a.tw, blockIdx.x, smem_raw);
 }
 
 // Pass 1 as a persistent pipeline (level grids whose pairs are a level's full
@@ -293,6 +302,42 @@ __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvA
 }
 
 // ---------------------------------------------------------------- passes 2, 4
+// tile: column tile (x); zs: slab index (z from the block's first input slab).
+// The indices are unsigned, as block indices are: the compiler then knows them
+// non-negative and keeps the address arithmetic of the kernel form.
+template <typename T, int P, int E, int TX, bool INV, int GM>
+__device__ __forceinline__ void ypass_body(cpx<T>* work, const cpx<T>* tw, unsigned tile, unsigned zs,
+                                           unsigned char* smem_raw) {
+    using G = Geo<P, E, GM>;
+    cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* sm_tile = sm_tw + P;
+    load_twiddles<P, E>(sm_tw, tw);
+    const int l = threadIdx.x % TX, j = threadIdx.x / TX;
+    // blockDim.x = TX P/E: lets the compiler see which outputs of the last
+    // pass the window keeps, and drop the rest
+    __builtin_assume(j < P / E);
+    const int z = (INV ? 0 : G::OFF) + zs;
+    const int x = tile * TX + l;
+    cpx<T>* slab = work + (size_t)z * P * P;
+    cpx<T> v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        if (INV || G::live(r)) v[r] = slab[(size_t)(j + r * (P / E)) * P + x];
+        else v[r] = {T(0), T(0)};
+    }
+    __syncthreads();
+    fft_line<T, P, E, INV, INV ? 0xFFFFu : G::LIVE, false>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const int e = out_index<P, E>(j, s);
+        if (!INV || e < G::NOUT) slab[(size_t)e * P + x] = v[s];
+    }
+}
+
+// The kernel form keeps its own copy of the body: calling ypass_body from it
+// compiled to a different register allocation that ran the passes 15-25 %
+// slower (ptxas: 42 against 48 registers at P = 256; measured 115 against
+// 97 us per y-forward at 6 x 128^3).  The arithmetic is the same.
 template <typename T, int P, int E, int TX, bool INV, int GM>
 __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ ConvArgs<T> a) {
     using G = Geo<P, E, GM>;
@@ -302,8 +347,6 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
     const PairDesc<T>& d = a.pair[blockIdx.z];
     load_twiddles<P, E>(sm_tw, a.tw);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
-    // blockDim.x = TX P/E: lets the compiler see which outputs of the last
-    // pass the window keeps, and drop the rest
     __builtin_assume(j < P / E);
     const int z = (INV ? 0 : G::OFF) + blockIdx.y;
     const int x = blockIdx.x * TX + l;
@@ -333,22 +376,21 @@ template <typename T, int NT> struct ZseamMinBlocks {
     static constexpr int value = R / NT > 0 ? R / NT : 1;
 };
 
+// tile: column tile (kx); y: the ky row
 template <typename T, int P, int E, int TX, int GM>
-__global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::value))
-    k_zseam(const __grid_constant__ ConvArgs<T> a) {
+__device__ __forceinline__ void zseam_body(const PairDesc<T>& d, const T* spec, const cpx<T>* tw, unsigned tile,
+                                           unsigned y,
+                                           unsigned char* smem_raw) {
     using G = Geo<P, E, GM>;
     constexpr int H = P / 2 + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
-    const PairDesc<T>& d = a.pair[blockIdx.z];
-    load_twiddles<P, E, true>(sm_tw, a.tw);
+    load_twiddles<P, E, true>(sm_tw, tw);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
     // blockDim.x = TX P/E: lets the compiler see which outputs of the last
     // pass the window keeps, and drop the rest
     __builtin_assume(j < P / E);
-    const int y = blockIdx.y;
-    const int x = blockIdx.x * TX + l;
+    const int x = tile * TX + l;
     cpx<T>* col = d.work + (size_t)y * P + x;          // element z at col[z * P * P]
     cpx<T> v[E];
 #pragma unroll
@@ -361,7 +403,7 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
     fft_line<T, P, E, false, G::LIVE, true, true>(v, j, sm_tw, view);
     const int fy = y <= P / 2 ? y : P - y;
     const int fx = x <= P / 2 ? x : P - x;
-    const T* sp = a.spec + (size_t)fy * H + fx;
+    const T* sp = spec + (size_t)fy * H + fx;
 #pragma unroll
     for (int s = 0; s < E; ++s) {
         const int kz = out_index<P, E>(j, s);
@@ -377,6 +419,13 @@ __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::va
         const int e = out_index<P, E>(j, s);
         if (e < G::NOUT) col[(size_t)e * P * P] = v[s];
     }
+}
+
+template <typename T, int P, int E, int TX, int GM>
+__global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::value))
+    k_zseam(const __grid_constant__ ConvArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    zseam_body<T, P, E, TX, GM>(a.pair[blockIdx.z], a.spec, a.tw, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // Pass 3 in FP32 with two neighbouring columns per thread.  The lines (ky, x)
@@ -474,17 +523,16 @@ __device__ __forceinline__ void store_out(const DstField& f, int z, int y, int x
 }
 
 template <typename T, int P, int E, int GM>
-__global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T> a) {
+__device__ __forceinline__ void xinv_body(const PairDesc<T>& d, const cpx<T>* tw, unsigned tile,
+                                          unsigned char* smem_raw) {
     constexpr int TPL = P / E;
     constexpr int LINES = 256 / TPL;
     constexpr int HALF = P / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
-    const PairDesc<T>& d = a.pair[blockIdx.y];
-    load_twiddles<P, E, true>(sm_tw, a.tw);
+    load_twiddles<P, E, true>(sm_tw, tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
-    const int row = blockIdx.x * LINES + line;
+    const int row = tile * LINES + line;
     const bool valid = row < HALF * HALF;
     const int z = row / HALF, y = row % HALF;
     cpx<T> v[E];
@@ -504,6 +552,12 @@ __global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T
             }
         }
     }
+}
+
+template <typename T, int P, int E, int GM>
+__global__ void __launch_bounds__(256) k_xinv(const __grid_constant__ ConvArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xinv_body<T, P, E, GM>(a.pair[blockIdx.y], a.tw, blockIdx.x, smem_raw);
 }
 
 // Column tile width of the strided passes: at most the requested width W,

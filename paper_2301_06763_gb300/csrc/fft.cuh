@@ -420,6 +420,11 @@ template <typename T, int ES, bool PAD, int LOGE = 4> struct LineView {
     }
     __device__ __forceinline__ cpx<T> ld(int e) const { return base[off(e)]; }
     __device__ __forceinline__ void st(int e, cpx<T> v) const { base[off(e)] = v; }
+    // the first pass's stores: elements E j + r, r < E
+    template <int E> __device__ __forceinline__ void st_first(int j, const cpx<T>* v) const {
+#pragma unroll
+        for (int r = 0; r < E; ++r) st(E * j + r, v[r]);
+    }
 };
 
 template <typename T, bool INV>
@@ -500,8 +505,7 @@ __device__ __forceinline__ void fft_line(cpx<T>* v, int j, const cpx<T>* tw, con
     static_assert(P >= E, "line shorter than the values a thread holds");
     dftRm<T, INV, E, M>(v);
     if constexpr (P > E) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) sm.st(E * j + r, v[r]);
+        sm.template st_first<E>(j, v);
         __syncthreads();
         fft_rest<T, P, E, INV, E, TAIL, PT>(v, j, tw, sm);
     }

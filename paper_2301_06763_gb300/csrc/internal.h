@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "conv.cuh"
 #include "per_device.h"
 #include "tma.cuh"
@@ -84,6 +86,19 @@ cudaError_t run_unfold_x(const double* in, float* out, int N, cudaStream_t s);
 // by the plan before its first paired z-seam), or null.
 const float* unfolded_spectrum(const float* spec);
 cudaError_t run_to_df(const double* in, df* out, size_t n, cudaStream_t s);
+// The octant as float with fz fastest ([fx][fy][fz], (N+1)^3 floats), read by
+// the fused y/z/y pass; and the copy belonging to the float octant `spec`
+// (built by the plan before its first three-pass solve), or null.
+cudaError_t run_zfast(const double* in, float* out, int N, cudaStream_t s);
+const float* zfast_spectrum(const float* spec);
+// Three-pass convolution (yzy.cuh) of npairs level-grid pairs, FP32, P = 2N in
+// 64 .. 512; `split` selects the CTAs per kx plane (0: the default for P, 1:
+// the alternative where one is built).  Pairs must be a level's full and hole
+// fields (or a full field alone) on a 16-byte aligned density.
+cudaError_t run_conv_f32_yzy(const PairDesc<float>* pairs, int npairs, int P, int split, const float* spec,
+                             const cpx<float>* tw, cudaStream_t s);
+// Whether run_conv_f32_yzy takes these pairs.
+bool yzy_pairs_ok(const PairDesc<float>* pairs, int npairs);
 
 // Restriction of level m+1 onto level m's covered cells (mean of 2^3 children).
 template <typename TIN>
@@ -133,6 +148,34 @@ template <typename T>
 cudaError_t run_reduce4(const T* in, T* out, int N, cudaStream_t s);
 template <typename T>
 cudaError_t run_direct2(const T* rho, const T* restr, T* out, int N, double scale, cudaStream_t s);
+
+// Persistent batch (persist.cu): every step of the FP32 original-method
+// solves of a batch as work items of one launch.  One mesh as the layout
+// needs it; `pairs` are its level pairs (work pointers unset), `asm_args` its
+// assembly arguments with the hole crops as interpolation sources, `carry`
+// the carried-interpolation scratch (diagonal reading) or null (trilinear).
+struct PersistMesh {
+    int P, L, group;
+    const float* rho;
+    float* restr;
+    double* phi;
+    void* work;
+    const float* spec;
+    const cpx<float>* tw;
+    std::vector<PairDesc<float>> pairs;
+    float* carry;
+    AssembleArgs<float> asm_args;
+};
+struct PersistBatch;
+PersistBatch* persist_new();
+void persist_free(PersistBatch* b);
+int persist_items(const PersistBatch* b);
+// Lay out the work items (host only; false if a mesh does not fit the path).
+bool persist_layout(const std::vector<PersistMesh>& meshes, PersistBatch& b);
+// Allocate and fill the device tables (synchronous: not while capturing).
+cudaError_t persist_upload(PersistBatch& b);
+// Reset the counters and launch on `s` (capturable).
+cudaError_t persist_launch(PersistBatch& b, cudaStream_t s);
 
 // g = -grad Phi of a nested potential (accel.cu).
 cudaError_t run_accel(const double* phi, double* g, int levels, int N, double dx0, cudaStream_t s);
