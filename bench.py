@@ -119,28 +119,41 @@ class ClockSampler:
 FP64_OPS_PEAK = 0.55e12
 
 
-def pass_bytes(name, N, fp32):
+def pass_bytes(name, N, fp32, half=False):
     """Algorithmic HBM bytes of one convolution pair in kernel `name` (level grid).
 
     The pass reads its input array once and writes its output once; the
-    density and spectrum are read once.  Level grid: N^3 block, P = 2N."""
+    density and spectrum are read once.  Level grid: N^3 block, P = 2N.
+    half: the pair carries one real field (the finest level of the original
+    method), whose x transform is Hermitian, so only the N + 1 columns
+    kx <= N of the work arrays are needed."""
     es = 4 if fp32 else 8
     cs = 2 * es
     P = 2 * N
     n3 = N ** 3
-    rows_in = N * N * P * cs           # [N][N][P] complex
-    slab = N * P * P * cs              # [N][P][P] complex
+    cols = (N + 1) if half else P      # kx columns the y, z and x-inverse passes need
+    rows_need = N * N * cols * cs      # [N][N][cols] complex (x-forward output)
+    slab = N * P * cols * cs           # [N][P][cols] complex
     if name.startswith("xfwd"):
-        return n3 * es + (N // 2) ** 3 * es + rows_in
+        return n3 * es + (N // 2) ** 3 * es + rows_need
     if name.startswith("yfwd"):
-        return rows_in + slab
+        return rows_need + slab
     if name.startswith("zseam"):
         return 2 * slab + (N + 1) ** 3 * es
     if name.startswith("yinv"):
-        return slab + rows_in
+        return slab + rows_need
     if name.startswith("xinv"):
-        return rows_in + n3 * es + (N // 2 + 2) ** 3 * es
+        return rows_need + n3 * es + (0 if half else (N // 2 + 2) ** 3 * es)
     return None
+
+
+def launch_bytes(name, N, fp32, pairs, solves):
+    """Algorithmic bytes of a launch of `name` covering `pairs` level pairs of
+    `solves` original-method solves: one real (half-spectrum) pair per solve."""
+    full = pass_bytes(name, N, fp32)
+    if full is None:
+        return None
+    return (pairs - solves) * full + solves * pass_bytes(name, N, fp32, half=True)
 
 
 # the sources whose kernels the traffic summary measures
@@ -162,8 +175,9 @@ def source_hash():
 
 
 def ncu_traffic(kernel_name):
-    """DRAM bytes per pair of `kernel_name` from the committed ncu summary, or
-    None when no summary exists or the kernel sources changed since."""
+    """(pairs, DRAM bytes per launch) of `kernel_name` from the committed ncu
+    summary, or None when no summary exists or the kernel sources changed
+    since."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.md")
     if not os.path.exists(path):
         return None
@@ -171,8 +185,8 @@ def ncu_traffic(kernel_name):
     m = re.search(r"source hash:\s*`?([0-9a-f]+)", text)
     if not m or m.group(1) != source_hash():
         return None
-    m = re.search(r"^\|\s*%s\s*\|[^|]*\|[^|]*\|\s*([0-9.e+]+)\s*\|" % re.escape(kernel_name), text, re.M)
-    return float(m.group(1)) if m else None
+    m = re.search(r"^\|\s*%s\s*\|\s*(\d+)\s*\|\s*([0-9.e+]+)\s*\|" % re.escape(kernel_name), text, re.M)
+    return (int(m.group(1)), float(m.group(2))) if m else None
 
 
 def peaks():
@@ -606,15 +620,18 @@ def ours(args):
     per_unit = pass_bytes(dname, N, True)
     roof = None
     if per_unit is not None:
-        bytes_launch = per_unit * du / dl
+        # each launch of a pass covers one solve: its L pairs, the finest a
+        # real (half-spectrum) pair
+        bytes_launch = launch_bytes(dname, N, True, du / dl, 1)
         achieved = bytes_launch / (dms / dl * 1e-3) / 1e9
-        per_pair = ncu_traffic(dname)
-        traffic = per_pair * du / dl if per_pair is not None else None
+        tr = ncu_traffic(dname)
+        # the summary's launches cover the benchmark's solves (L pairs each)
+        traffic = tr[1] if tr is not None and tr[0] == round(du / dl) else None
         roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "algorithmic_bytes_per_launch": bytes_launch,
                 "avg_launch_ms": dms / dl}
-    solve_bytes = sum(pass_bytes(k, N, True) * v[1] for k, v in stats.items()
+    solve_bytes = sum(launch_bytes(k, N, True, v[1], v[0]) for k, v in stats.items()
                       if pass_bytes(k, N, True) is not None) / args.steps
     kernel_table = {k: {"launches": v[0], "avg_ms": v[2] / v[0], "share": v[2] / sum(
         x[2] for x in stats.values())} for k, v in sorted(stats.items(), key=lambda kv: -kv[1][2])}
@@ -789,6 +806,41 @@ def serve_mode(args):
         dens[N] = torch.from_numpy(np.ascontiguousarray(w.rho().astype(np.float32))).pin_memory()
     free, total = torch.cuda.mem_get_info()
     budget = int(0.5 * free)
+    srv = Server(budget, slots=4, precision="fp32", per_shape_cap=2)
+    # plans, spectra and buffers for every shape of the request distribution,
+    # made once before the streams start (untimed); with at most 2 sets per
+    # shape in existence the request loop then allocates nothing
+    shapes = [(L, N) for N in (32, 64, 128, 256) for L in range(3, 11)]
+    srv.prewarm(shapes, per_shape=2)
+    made0 = srv.residents_made
+    # the device-bound rate of the mix: per shape, the solve alone and the
+    # solve with its upload and download, on a resident set, timed by events
+    per_shape = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for (L, N) in shapes:
+        key = (L, N, 1.0 / N, 1.0, "original")
+        res = srv._pool_take(key)
+        if res is None:
+            continue
+        for _ in range(3):
+            res.plan.potential(res.rho_dev, res.phi_dev)
+        torch.cuda.synchronize()
+        reps = 10 if N < 256 else 4
+        ev[0].record()
+        for _ in range(reps):
+            res.plan.potential(res.rho_dev, res.phi_dev)
+        ev[1].record()
+        for _ in range(reps):
+            res.rho_dev.copy_(dens[N][:L], non_blocking=True)
+            res.plan.potential(res.rho_dev, res.phi_dev)
+            res.phi_pin.copy_(res.phi_dev, non_blocking=True)
+        ev[2].record()
+        torch.cuda.synchronize()
+        per_shape["%dx%d" % (L, N)] = {"solve_ms": ev[0].elapsed_time(ev[1]) / reps,
+                                       "with_copies_ms": ev[1].elapsed_time(ev[2]) / reps}
+        srv._pool_put(res)
+    mix_solve = float(np.mean([v["solve_ms"] for v in per_shape.values()]))
+    mix_copies = float(np.mean([v["with_copies_ms"] for v in per_shape.values()]))
     results = []
     for rate in [float(x) for x in args.rates.split(",")]:
         count = int(min(2000, max(20, rate * args.serve_seconds)))
@@ -797,31 +849,29 @@ def serve_mode(args):
         for i, (t, w) in enumerate(arrivals):
             reqs.append(Request(i, w.levels, w.N, w.dx0, dens[w.N][:w.levels], arrival=t,
                                 keep_result=False))
-        srv = Server(budget, slots=4, precision="fp32")
-        # plans, spectra and buffers for every shape of the request
-        # distribution, made before the stream starts (untimed), then one
-        # untimed request per shape so that each shape's solve graph exists
-        shapes = [(L, N) for N in (32, 64, 128, 256) for L in range(3, 11)]
-        srv.prewarm(shapes, per_shape=3)
-        made0 = srv.residents_made
-        warm = [Request(-1 - i, L, N, 1.0 / N, dens[N][:L], keep_result=False)
-                for i, (L, N) in enumerate(sorted(set((r.levels, r.N) for r in reqs)))]
-        run_stream(srv, warm)
         srv.completed.clear()
+        srv.failed.clear()
+        srv.batches = 0
         made1 = srv.residents_made
         elapsed, done = run_stream(srv, reqs)
         st = latency_stats(done)
         results.append({"rate": rate, "requests": count, "completed": len(done),
                         "failed": len(srv.failed), "solves_per_s": len(done) / elapsed,
                         "batches": srv.batches, "peak_bytes": srv.peak_used,
-                        "residents_prewarmed": made0, "residents_made_while_serving": srv.residents_made - made1,
-                        **st})
-        srv.close()
-        torch.cuda.empty_cache()
+                        "residents_made_while_serving": srv.residents_made - made1, **st})
+    srv.close()
+    torch.cuda.empty_cache()
     print(json.dumps({"mode": "serve", "metric": "served solves/s and latency (arrival -> host potentials)",
                       "unit": "solves/s", "budget_bytes": budget, "precision": "fp32",
                       "requests": "N in {32,64,128,256}, 3-10 levels, Poisson arrivals",
                       "density": "one seeded 1-4 Plummer density per N, sliced to the level count",
+                      "residents_prewarmed": made0,
+                      "device_bound": {"mix_solve_ms": mix_solve, "mix_solve_rate": 1e3 / mix_solve,
+                                       "mix_with_copies_ms": mix_copies, "mix_with_copies_rate": 1e3 / mix_copies,
+                                       "what": "mean over the 32 request shapes (uniform N and L) of one solve "
+                                               "alone and of one solve with its upload and download, one at a "
+                                               "time on one stream"},
+                      "per_shape": per_shape,
                       "rates": results}))
 
 

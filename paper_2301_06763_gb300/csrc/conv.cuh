@@ -50,6 +50,13 @@ template <typename T> struct PairDesc {
     cpx<T>* work;
     SrcField src[2];
     DstField dst[2];
+    // 1: the pair carries one real field (its second slot is empty, as for
+    // the finest level of Eq. 14).  Its transform along x is then Hermitian,
+    // X[P - kx] = conj X[kx], and so is every (z, y) row of the result: the
+    // y and z passes skip the column tiles above kx = P/2 and the x-inverse
+    // reads kx > P/2 as conj X[P - kx].  Set by the launcher for the
+    // schedules that honour it; 0 everywhere else.
+    int half;
 };
 
 constexpr int kMaxPairs = 64;
@@ -345,6 +352,7 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
     const PairDesc<T>& d = a.pair[blockIdx.z];
+    if (d.half && blockIdx.x * TX > P / 2) return;   // the column tile is above kx = P/2 (whole CTA)
     load_twiddles<P, E>(sm_tw, a.tw);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
     __builtin_assume(j < P / E);
@@ -425,6 +433,7 @@ template <typename T, int P, int E, int TX, int GM>
 __global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<T, TX * P / E>::value))
     k_zseam(const __grid_constant__ ConvArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.pair[blockIdx.z].half && blockIdx.x * TX > P / 2) return;   // above kx = P/2 (whole CTA)
     zseam_body<T, P, E, TX, GM>(a.pair[blockIdx.z], a.spec, a.tw, blockIdx.x, blockIdx.y, smem_raw);
 }
 
@@ -458,6 +467,7 @@ __global__ void __launch_bounds__(TX / 2 * P / E, Zseam2MinBlocks<TX / 2 * P / E
     cpx<f2>* sm_tile = sm_tw + P;
     float* sm_sp = reinterpret_cast<float*>(sm_tile + TX2 * P);      // [H][TX]
     const PairDesc<float>& d = a.pair[blockIdx.z];
+    if (d.half && blockIdx.x * TX > P / 2) return;   // above kx = P/2 (whole CTA)
     const int y = blockIdx.y;
     const int fy = y <= P / 2 ? y : P - y;
     {
@@ -537,8 +547,17 @@ __device__ __forceinline__ void xinv_body(const PairDesc<T>& d, const cpx<T>* tw
     const int z = row / HALF, y = row % HALF;
     cpx<T> v[E];
     const cpx<T>* src = d.work + ((size_t)z * P + y) * P;
+    // a real pair (d.half): only kx <= P/2 went through the y and z passes,
+    // and kx > P/2 is read as conj X[P - kx]
+    const bool half = d.half != 0;
 #pragma unroll
-    for (int r = 0; r < E; ++r) v[r] = valid ? src[j + r * (P / E)] : cpx<T>{T(0), T(0)};
+    for (int r = 0; r < E; ++r) {
+        const int kx = j + r * (P / E);
+        const bool up = half && kx > P / 2;
+        cpx<T> w = valid ? src[up ? P - kx : kx] : cpx<T>{T(0), T(0)};
+        if (up) w.im = -w.im;
+        v[r] = w;
+    }
     __syncthreads();
     fft_line<T, P, E, true, 0xFFFFu, false, true>(v, j, sm_tw,
                                             LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});

@@ -292,9 +292,15 @@ static cudaError_t run_conv_variant(const PairDesc<T>* pairs, int npairs, int P,
     ConvArgs<T> a;
     a.spec = spec;
     a.tw = tw;
+    // real pairs (one field, second slot empty) take the half-spectrum path
+    // on level grids with the separate y and z passes
+    const bool halves = !dbl && !(flags & (CONV_TMA | CONV_FUSED));
     for (int i0 = 0; i0 < npairs; i0 += kMaxPairs) {
         const int np = npairs - i0 < kMaxPairs ? npairs - i0 : kMaxPairs;
-        for (int i = 0; i < np; ++i) a.pair[i] = pairs[i0 + i];
+        for (int i = 0; i < np; ++i) {
+            a.pair[i] = pairs[i0 + i];
+            a.pair[i].half = (halves && a.pair[i].src[0].mode != SRC_NONE && a.pair[i].src[1].mode == SRC_NONE) ? 1 : 0;
+        }
         cudaError_t e = conv_dispatch<T, E>(a, np, P, dbl, flags, s);
         if (e != cudaSuccess) return e;
     }

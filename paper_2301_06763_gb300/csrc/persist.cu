@@ -133,8 +133,11 @@ __device__ __forceinline__ void restrict_item(const PRestrict& r, int tile) {
     r.out[2 * i + 1] = s1 * 0.125f;
 }
 
-// The restriction, carry and assembly steps are light per 256-thread tile, so
-// one of their items does kSub consecutive tiles.
+// The assembly is light per 256-thread tile, so one of its items does kSub
+// consecutive tiles.  The restriction and carry steps stay at one tile per
+// item: each level of theirs waits for the previous one, and bigger items
+// would lengthen that chain (measured: 0.79 -> 1.0 ms per 6 x 128^3 solve with
+// 8 tiles per restriction and carry item).
 constexpr int kSub = 8;
 
 // Columns per item of the column passes: 256 threads of P / 16 per column.
@@ -213,12 +216,10 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist(const __grid_con
             }
             const int tile = item - sg.first;
             switch (sg.kind) {
-                case PK_RESTRICT:
-                    for (int u = 0; u < kSub; ++u) restrict_item(t.rs[sg.arg], tile * kSub + u);
-                    break;
+                case PK_RESTRICT: restrict_item(t.rs[sg.arg], tile); break;
                 case PK_CARRY:
-                    carry_body<float>(t.carry[sg.arg], (size_t)tile * kSub * kPersistThreads + threadIdx.x,
-                                      kPersistThreads, (size_t)(tile + 1) * kSub * kPersistThreads);
+                    carry_body<float>(t.carry[sg.arg], (size_t)tile * kPersistThreads + threadIdx.x,
+                                      kPersistThreads, (size_t)(tile + 1) * kPersistThreads);
                     break;
                 case PK_ASSEMBLE: {
                     const PAsm& pa = t.as[sg.arg];
@@ -317,7 +318,7 @@ bool persist_layout(const std::vector<PersistMesh>& meshes, PersistBatch& b) {
         const PersistMesh& m = meshes[i];
         const int N = m.P / 2, h = N / 2;
         const size_t N3 = (size_t)N * N * N, h3 = (size_t)h * h * h;
-        const int tiles = (int)((h3 / 2 + (size_t)kSub * kPersistThreads - 1) / ((size_t)kSub * kPersistThreads));
+        const int tiles = (int)((h3 / 2 + kPersistThreads - 1) / kPersistThreads);
         for (int lv = m.L - 2; lv >= 0; --lv) {
             PRestrict r;
             r.child = m.rho + (size_t)(lv + 1) * N3;
@@ -415,7 +416,7 @@ bool persist_layout(const std::vector<PersistMesh>& meshes, PersistBatch& b) {
             b.carry.push_back(c);
             const int wprev = n == 1 ? xi_seg[i * NM_MAX_LEVELS + 0] : ca_seg[i * NM_MAX_LEVELS + n - 1];
             const int whole = xi_seg[i * NM_MAX_LEVELS + n];
-            const int tiles = (int)((nc3 + (size_t)kSub * kPersistThreads - 1) / ((size_t)kSub * kPersistThreads));
+            const int tiles = (int)((nc3 + kPersistThreads - 1) / kPersistThreads);
             const int id = add(PK_CARRY, N, (int)b.carry.size() - 1, tiles, wprev, b.seg[wprev].tiles, whole,
                                b.seg[whole].tiles, -2, -1);
             b.seg[id].done[0] = id;

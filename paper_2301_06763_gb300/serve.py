@@ -79,7 +79,8 @@ class _Resident:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes, slots=4, precision="fp32", max_batch=64, device=None, interp="diagonal"):
+    def __init__(self, hbm_budget_bytes, slots=4, precision="fp32", max_batch=64, device=None, interp="diagonal",
+                 per_shape_cap=None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -99,6 +100,9 @@ class Server:
         self.failed = []
         self.batches = 0
         self.residents_made = 0
+        self.res_count = {}                     # key -> resident sets in existence
+        self.per_shape_cap = int(per_shape_cap if per_shape_cap is not None else slots)
+        self.scan_limit = 4 * self.max_batch
 
     # ------------------------------------------------------------------ memory
     def _dtype(self):
@@ -137,7 +141,7 @@ class Server:
             key, lst = next(iter(self.pool.items()))
             res = lst.pop()
             self.pool_bytes -= res.bytes
-            res.close()
+            self._close(res)
             if not lst:
                 del self.pool[key]
         return self.used + self.pool_bytes + need <= self.budget
@@ -145,7 +149,12 @@ class Server:
     def _make(self, key):
         res = _Resident(self.torch, key, self.precision, self.interp, self.device)
         self.residents_made += 1
+        self.res_count[key] = self.res_count.get(key, 0) + 1
         return res
+
+    def _close(self, res):
+        self.res_count[res.key] = self.res_count.get(res.key, 1) - 1
+        res.close()
 
     def prewarm(self, shapes, per_shape=1, method="original", G=1.0):
         """Make plans, Green spectra and buffers for request shapes ahead of
@@ -195,20 +204,29 @@ class Server:
         self.inflight = keep
 
     def _admit(self):
+        """Requests for the next batch, oldest first.  A request whose shape
+        has no idle resident set is admitted with a new one only while that
+        shape has fewer than `per_shape_cap` sets; otherwise it waits in the
+        queue (later requests of other shapes may pass it), so a warm server
+        allocates nothing however many requests of one shape are queued."""
         batch = []
-        while self.queue and len(batch) < self.max_batch:
-            r = self.queue[0]
+        keep = collections.deque()
+        scanned = 0
+        while self.queue and len(batch) < self.max_batch and scanned < self.scan_limit:
+            r = self.queue.popleft()
+            scanned += 1
             key = self._key(r)
             res = self._pool_take(key)
+            if res is None and self.res_count.get(key, 0) >= self.per_shape_cap:
+                keep.append(r)                  # all of this shape's sets are in flight
+                continue
             try:
                 need = res.bytes if res is not None else self.request_bytes(r)
-            except Exception as e:          # invalid shape: rejected by the library
-                self.queue.popleft()
+            except Exception as e:              # invalid shape: rejected by the library
                 r.error = str(e)
                 self.failed.append(r)
                 continue
             if need > self.budget:
-                self.queue.popleft()
                 r.error = "footprint %d bytes exceeds the HBM budget %d" % (need, self.budget)
                 if res is not None:
                     self._pool_put(res)
@@ -217,12 +235,12 @@ class Server:
             if not self._evict_until(need):
                 if res is not None:
                     self._pool_put(res)
+                keep.append(r)
                 break
-            self.queue.popleft()
             if res is None:
                 try:
                     res = self._make(key)
-                except Exception as e:      # invalid shape or allocation failure
+                except Exception as e:          # invalid shape or allocation failure
                     r.error = str(e)
                     self.failed.append(r)
                     continue
@@ -233,6 +251,9 @@ class Server:
             self.peak_used = max(self.peak_used, self.used + self.pool_bytes)
             r.admitted = time.perf_counter()
             batch.append(r)
+        # the passed-over requests keep their places at the head of the queue
+        keep.extend(self.queue)
+        self.queue = keep
         return batch
 
     def step(self):
@@ -280,7 +301,7 @@ class Server:
         self.drain()
         for lst in self.pool.values():
             for res in lst:
-                res.close()
+                self._close(res)
         self.pool.clear()
         self.pool_bytes = 0
 

@@ -56,13 +56,23 @@ def test_traffic_summary_follows_the_kernel_sources(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     base = bench.source_hash()
     (tmp_path / "profiles" / "ncu_traffic.md").write_text(
-        "source hash: `%s`\n\n| kernel | a | b | bytes per pair |\n|---|---|---|---|\n"
-        "| zseam_f32_P256 | x | y | 1.25e8 |\n" % base)
-    assert bench.ncu_traffic("zseam_f32_P256") == 1.25e8
+        "source hash: `%s`\n\n| kernel | pairs | bytes per launch | c |\n|---|---|---|---|\n"
+        "| zseam_f32_P256 | 6 | 7.5e8 | y |\n" % base)
+    assert bench.ncu_traffic("zseam_f32_P256") == (6, 7.5e8)
     conv = csrc / "conv.cuh"
     conv.write_text("// a new comment\n" + conv.read_text().replace("namespace nm {", "namespace nm {\n\n/* block */ ", 1))
     assert bench.source_hash() == base
-    assert bench.ncu_traffic("zseam_f32_P256") == 1.25e8
+    assert bench.ncu_traffic("zseam_f32_P256") == (6, 7.5e8)
     conv.write_text(conv.read_text().replace("constexpr int kMaxPairs = 64;", "constexpr int kMaxPairs = 65;"))
     assert bench.source_hash() != base
     assert bench.ncu_traffic("zseam_f32_P256") is None
+
+
+def test_launch_bytes_count_one_half_pair_per_solve():
+    # the finest pair of an original-method solve needs only kx <= N
+    N = 128
+    full = bench.pass_bytes("zseam_f32_P256", N, True)
+    half = bench.pass_bytes("zseam_f32_P256", N, True, half=True)
+    assert half < full and abs(half - (2 * N * 2 * N * (N + 1) * 8 + (N + 1) ** 3 * 4)) == 0
+    assert bench.launch_bytes("zseam_f32_P256", N, True, 6, 1) == 5 * full + half
+    assert bench.launch_bytes("restrict_f32", N, True, 5, 5) is None
