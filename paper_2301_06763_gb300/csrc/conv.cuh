@@ -308,6 +308,98 @@ __global__ void __launch_bounds__(256) k_xfwd_pipe(const __grid_constant__ ConvA
     }
 }
 
+// Pass 1 as the persistent pipeline with two rows per thread (FP32 density):
+// rows (z, y) and (z, y + 1), y even, go through identical arithmetic, so the
+// thread carries them as one transform over cpx<f2> (lane 0 = row y, lane 1 =
+// row y + 1), as the paired z-seam does for two columns; each shared-memory
+// access and twiddle read then serves both rows.  128 threads = the LINES / 2 row pairs of one staged tile.  A real
+// pair (d.half) writes only the columns the y and z passes read (kx < P/2 +
+// 32: up to the widest column tile holding kx = P/2).
+template <int P>
+__global__ void __launch_bounds__(128, 4) k_xfwd_pipe2(const __grid_constant__ ConvArgs<float> a, int npairs) {
+    using T = float;
+    using TIN = float;
+    constexpr int E = 16;
+    using G = Geo<P, E, 0>;
+    using S = XfwdStage<TIN, P, E>;
+    constexpr int TPL = P / E, LINES = 256 / TPL, LP = LINES / 2, NIN = G::NIN;
+    constexpr int TILE = LINES * NIN;
+    constexpr int TILES = NIN * NIN / LINES;
+    constexpr int VEC = 4;
+    static_assert((NIN * NIN) % LINES == 0 && TILE % (128 * VEC) == 0 && NIN % VEC == 0 && LP * TPL == 128,
+                  "tile shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<f2>* sm_tw = reinterpret_cast<cpx<f2>*>(smem_raw);
+    cpx<f2>* sm_lines = sm_tw + P;
+    TIN* stage = reinterpret_cast<TIN*>(sm_lines + LP * (P + P / E));   // [2][LINES][PITCH]
+    fill_pass_twiddles<P, E>(sm_tw, [&](int t) {
+        const cpx<float> w = a.tw[t];
+        return cpx<f2>{f2(w.re, w.re), f2(w.im, w.im)};
+    });
+    const int lp = threadIdx.x / TPL, j = threadIdx.x % TPL;
+    const int total = npairs * TILES;
+    auto issue = [&](int t, int b) {
+        const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
+        const TIN* src = (const TIN*)a.pair[pr].src[0].rho + (size_t)row0 * NIN;
+        TIN* dst = stage + b * S::ELEMS;
+#pragma unroll
+        for (int i = threadIdx.x * VEC; i < TILE; i += 128 * VEC) {
+            const int row = i / NIN;
+            cp_async16(dst + row * S::PITCH + (i - row * NIN), src + i);
+        }
+    };
+    int t = blockIdx.x;
+    if (t < total) issue(t, 0);
+    cp_async_commit();
+    for (int k = 0; t < total; ++k, t += gridDim.x) {
+        if (t + (int)gridDim.x < total) issue(t + gridDim.x, (k + 1) & 1);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int pr = t / TILES, row0 = (t - pr * TILES) * LINES;
+        const PairDesc<T>& d = a.pair[pr];
+        const T s0 = (T)d.src[0].scale, s1 = (T)d.src[1].scale;
+        const int row = row0 + 2 * lp;                      // rows row, row + 1: same z, y even
+        const int zi = row / NIN, yi = row % NIN;
+        const int q = NIN / 4, h = NIN / 2;
+        const bool zc = (unsigned)(zi - q) < (unsigned)h;
+        const bool cov0 = zc && (unsigned)(yi - q) < (unsigned)h;
+        const bool cov1 = zc && (unsigned)(yi + 1 - q) < (unsigned)h;
+        const bool hole = d.src[1].mode == SRC_HOLE;
+        const TIN* st = stage + (k & 1) * S::ELEMS + 2 * lp * S::PITCH;
+        const TIN* rs = (const TIN*)d.src[0].restr;
+        cpx<f2> v[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            v[r] = {f2(0), f2(0)};
+            if (G::live(r)) {
+                const int xi = j + r * (P / E);
+                const bool xc = (unsigned)(xi - q) < (unsigned)h;
+                const T a0 = st[xi], a1 = st[S::PITCH + xi];
+                T f0 = a0, f1 = a1;
+                if (rs && cov0 && xc) f0 = rs[((size_t)(zi - q) * h + (yi - q)) * h + (xi - q)];
+                if (rs && cov1 && xc) f1 = rs[((size_t)(zi - q) * h + (yi + 1 - q)) * h + (xi - q)];
+                v[r].re = f2(f0 * s0, f1 * s0);
+                v[r].im = f2((hole && !(cov0 && xc)) ? a0 * s1 : T(0), (hole && !(cov1 && xc)) ? a1 * s1 : T(0));
+            }
+        }
+        fft_line<f2, P, E, false, G::LIVE, false, true>(v, j, sm_tw,
+                                                  LineView<f2, 1, true, Log2E<E>::value>{sm_lines + lp * (P + P / E)});
+        cpx<T>* out0 = d.work + ((size_t)zi * P + yi) * P;
+        cpx<T>* out1 = out0 + P;
+        const int kx_end = d.half ? P / 2 + 32 : P;
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            const int kx = out_index<P, E>(j, s);
+            if (kx < kx_end) {
+                out0[kx] = {v[s].re.x, v[s].im.x};
+                out1[kx] = {v[s].re.y, v[s].im.y};
+            }
+        }
+        __syncthreads();   // this half of the stage and the line scratch are free again
+    }
+}
+
 // ---------------------------------------------------------------- passes 2, 4
 // tile: column tile (x); zs: slab index (z from the block's first input slab).
 // The indices are unsigned, as block indices are: the compiler then knows them

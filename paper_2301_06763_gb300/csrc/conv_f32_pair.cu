@@ -39,6 +39,35 @@ static cudaError_t zseam2_p(const ConvArgs<float>& a, int np, int P, cudaStream_
     }
 }
 
+template <int P>
+static cudaError_t launch_xfwd2(const ConvArgs<float>& a, int np, cudaStream_t s) {
+    constexpr int E = 16, TPL = P / E, LINES = 256 / TPL, LP = LINES / 2, N = P / 2;
+    const size_t smem = (size_t)P * sizeof(cpx<f2>) + (size_t)LP * (P + P / E) * sizeof(cpx<f2>) +
+                        2 * (size_t)XfwdStage<float, P, E>::ELEMS * sizeof(float);
+    static PerDevice<KernelPrep> prep;   // shared-memory limit and resident CTAs per SM, once per device
+    const KernelPrep kp = prep.get(current_device(), [&]() {
+        KernelPrep r;
+        r.err = cudaFuncSetAttribute(k_xfwd_pipe2<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r.err == cudaSuccess)
+            r.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.occ, k_xfwd_pipe2<P>, 128, smem);
+        return r;
+    }, KernelPrep{cudaErrorInvalidDevice, 0});
+    if (kp.err != cudaSuccess) return kp.err;
+    const int tiles = np * (N * N / LINES);
+    int grid = (kp.occ > 0 ? kp.occ : 1) * sm_count();
+    if (grid > tiles) grid = tiles;
+    k_xfwd_pipe2<P><<<grid, 128, smem, s>>>(a, np);
+    return cudaGetLastError();
+}
+
+cudaError_t run_xfwd_paired_f32(const ConvArgs<float>& a, int np, int P, cudaStream_t s) {
+    switch (P) {
+        case 256: return launch_xfwd2<256>(a, np, s);
+        case 512: return launch_xfwd2<512>(a, np, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t run_zseam_paired_f32(const ConvArgs<float>& a, int np, int P, int TX, cudaStream_t s) {
     if (TX == 16) return zseam2_p<16>(a, np, P, s);
     if (TX == 32) return zseam2_p<32>(a, np, P, s);

@@ -48,6 +48,10 @@ struct ProfScope {
 enum { CONV_WIDE = 1, CONV_TMA = 2, CONV_FUSED = 4, CONV_PAIRED = 8 };
 // k_zseam2 over np pairs of FFT size P with TX columns per CTA (16 or 32).
 cudaError_t run_zseam_paired_f32(const ConvArgs<float>& a, int np, int P, int TX, cudaStream_t s);
+// k_xfwd_pipe2 (two rows per thread) over np pairs of FFT size P (256 or
+// 512); needs pairs of a level's full and hole fields (or a full field alone)
+// on a 16-byte aligned FP32 density.
+cudaError_t run_xfwd_paired_f32(const ConvArgs<float>& a, int np, int P, cudaStream_t s);
 cudaError_t run_conv_f32_e16(const PairDesc<float>* pairs, int npairs, int P, bool dbl, int flags,
                              const float* spec, const cpx<float>* tw, cudaStream_t s);
 cudaError_t run_conv_f32_e8(const PairDesc<float>* pairs, int npairs, int P, bool dbl, int flags,

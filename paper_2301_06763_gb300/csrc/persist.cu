@@ -43,6 +43,7 @@ struct PSeg {
     int first;          // ticket of its first item
     int wait[2], need[2];   // counters to wait for (-1: none) and the counts they must reach
     int done[2];        // counters bumped by each finished item (-1: none)
+    int xt;             // column passes: x tiles per row (fewer for a real pair's half spectrum)
 };
 struct PPair {
     PairDesc<float> d;
@@ -146,8 +147,8 @@ template <int P> struct PCols {
 };
 
 template <int P>
-__device__ __forceinline__ void transform_item(int kind, const PPair& pp, int tile, unsigned char* smem) {
-    constexpr int E = 16, TX = PCols<P>::TX, XT = P / TX;
+__device__ __forceinline__ void transform_item(int kind, const PPair& pp, int tile, int XT, unsigned char* smem) {
+    constexpr int E = 16, TX = PCols<P>::TX;
     switch (kind) {
         case PK_XFWD: xfwd_body<float, float, P, E, 0>(pp.d, pp.tw, tile, smem); break;
         case PK_YFWD: ypass_body<float, P, E, TX, false, 0>(pp.d.work, pp.tw, tile % XT, tile / XT, smem); break;
@@ -235,10 +236,10 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist(const __grid_con
                 default: {
                     const PPair& pp = t.pair[sg.arg];
                     switch (sg.P) {
-                        case 64: transform_item<64>(sg.kind, pp, tile, smem); break;
-                        case 128: transform_item<128>(sg.kind, pp, tile, smem); break;
-                        case 256: transform_item<256>(sg.kind, pp, tile, smem); break;
-                        default: transform_item<512>(sg.kind, pp, tile, smem); break;
+                        case 64: transform_item<64>(sg.kind, pp, tile, sg.xt, smem); break;
+                        case 128: transform_item<128>(sg.kind, pp, tile, sg.xt, smem); break;
+                        case 256: transform_item<256>(sg.kind, pp, tile, sg.xt, smem); break;
+                        default: transform_item<512>(sg.kind, pp, tile, sg.xt, smem); break;
                     }
                 }
             }
@@ -352,6 +353,9 @@ bool persist_layout(const std::vector<PersistMesh>& meshes, PersistBatch& b) {
                     const int pi = pair_base[i] + q;
                     PPair& pp = b.pair[pi];
                     pp.d.work = (cpx<float>*)m.work + (size_t)(q - r * m.group) * (size_t)(P / 2) * P * P;
+                    // a real pair: the column passes stop at the tile holding kx = N
+                    pp.d.half = pp.d.src[1].mode == SRC_NONE ? 1 : 0;
+                    const int XT = pp.d.half ? (P / 2) / TX + 1 : P / TX;
                     int kind = PK_XFWD + pass, tiles = 0, w0 = -1, n0 = 0, w1 = -1, n1 = 0;
                     switch (kind) {
                         case PK_XFWD:
@@ -367,9 +371,9 @@ bool persist_layout(const std::vector<PersistMesh>& meshes, PersistBatch& b) {
                                 n1 = b.seg[w1].tiles;
                             }
                             break;
-                        case PK_YFWD: tiles = (P / TX) * N; break;
-                        case PK_ZSEAM: tiles = (P / TX) * P; break;
-                        case PK_YINV: tiles = (P / TX) * N; break;
+                        case PK_YFWD: tiles = XT * N; break;
+                        case PK_ZSEAM: tiles = XT * P; break;
+                        case PK_YINV: tiles = XT * N; break;
                         default: tiles = N * N / LINES; break;
                     }
                     if (pass > 0) {
@@ -378,6 +382,7 @@ bool persist_layout(const std::vector<PersistMesh>& meshes, PersistBatch& b) {
                     }
                     const int id = add(kind, P, pi, tiles, w0, n0, w1, n1, -2, -1);
                     b.seg[id].done[0] = id;
+                    b.seg[id].xt = XT;
                     seg_of[(size_t)pi * 5 + pass] = id;
                     if (kind == PK_XINV) {
                         xi_seg[i * NM_MAX_LEVELS + q] = id;
