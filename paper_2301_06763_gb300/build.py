@@ -17,7 +17,8 @@ LIB = os.path.join(HERE, "libnestconv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["conv_f32_e16.cu", "conv_f32_e8.cu", "conv_f64_e16.cu", "conv_f64_e8.cu", "support.cu",
          "api.cu", "noalloc.cu", "accel.cu", "conv_f32_qdp.cu", "conv_f64_qdp.cu", "dipole3.cu",
-         "conv_dfx_e16.cu", "fft_check.cu", "conv_f32_pair.cu", "conv_f32_yzy.cu", "persist.cu"]
+         "conv_dfx_e16.cu", "fft_check.cu", "conv_f32_pair.cu", "conv_f32_yzy.cu", "persist.cu",
+         "chains.cu"]
 
 
 def nvcc():

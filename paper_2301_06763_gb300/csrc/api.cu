@@ -984,12 +984,74 @@ nm_status enqueue_assemble(nm_plan_t p, double* phi, cudaStream_t s) {
     return NM_OK;
 }
 
+
 // One mesh of a batch (or a single solve).
 struct Item {
     nm_plan_t p;
     const void* rho;
     double* phi;
 };
+
+// The restrictions of every mesh of a batch: one launch for all their levels
+// (chains.cu), the per-level kernel where a mesh is too small or too deep.
+template <typename T>
+nm_status enqueue_restrict_batch(const std::vector<Item>& items, cudaStream_t s) {
+    using TIN = typename InOf<T>::type;
+    std::vector<RestrictMesh<TIN>> rm;
+    for (const Item& it : items)
+        if (it.p->L >= 2) rm.push_back({(const TIN*)it.rho, (TIN*)it.p->restr, it.p->N, it.p->L});
+    if (rm.empty()) return NM_OK;
+    cudaError_t e = run_restrict_tree<TIN>(rm.data(), (int)rm.size(), s);
+    if (e != cudaSuccess) return cuda_fail(e, "restriction");
+    return NM_OK;
+}
+
+// The carried interpolation of every mesh of a batch that reads the Eqs. 3-6
+// rule (one launch for all their levels), then each mesh's assembly reading
+// the carried sums.
+template <typename T>
+nm_status enqueue_assemble_batch(const std::vector<Item>& items, cudaStream_t s) {
+    std::vector<CarryMesh<T>> cm;
+    for (const Item& it : items) {
+        nm_plan_t p = it.p;
+        if (p->opt.interp != NM_INTERP_DIAGONAL || p->L < 3) continue;
+        const AssembleArgs<T> a = assemble_args<T>(p, it.phi);
+        const size_t N3 = (size_t)p->N * p->N * p->N, nc = p->N / 2 + 2;
+        CarryMesh<T> m{};
+        m.hole = a.interp[0];
+        m.hole_stride = p->dipole ? N3 : nc * nc * nc;
+        m.hole_origin = a.interp_origin[0];
+        m.hole_extent = a.interp_extent[0];
+        m.out = (T*)p->carry;
+        m.N = p->N;
+        m.L = p->L;
+        cm.push_back(m);
+    }
+    if (!cm.empty()) {
+        cudaError_t e = run_carry_tree<T>(cm.data(), (int)cm.size(), s);
+        if (e != cudaSuccess) return cuda_fail(e, "carried interpolation");
+    }
+    std::vector<AssembleArgs<T>> as;
+    for (const Item& it : items) {
+        nm_plan_t p = it.p;
+        AssembleArgs<T> a = assemble_args<T>(p, it.phi);
+        if (p->opt.interp == NM_INTERP_DIAGONAL) {
+            const int N = p->N;
+            const size_t nc = N / 2 + 2, nc3 = nc * nc * nc;
+            a.diag = 1;
+            for (int n = 1; n + 1 < p->L; ++n) {
+                a.interp[n] = (const T*)p->carry + (size_t)(n - 1) * nc3;
+                a.interp_origin[n] = N / 4 - 1;
+                a.interp_extent[n] = (int)nc;
+            }
+        }
+        as.push_back(a);
+    }
+    // one mesh: the single-mesh kernel; several: one launch per kAsmMeshes
+    cudaError_t e = as.size() == 1 ? run_assemble<T>(as[0], s) : run_assemble_batch<T>(as.data(), (int)as.size(), s);
+    if (e != cudaSuccess) return cuda_fail(e, "assembly");
+    return NM_OK;
+}
 
 // The solves of plans with the persistent schedule (fuse 3): one laid-out
 // batch per set of (plan, rho, phi), built on first use (synchronously, so
@@ -1110,8 +1172,7 @@ nm_status enqueue_items(const std::vector<Item>& items, cudaStream_t s) {
 template <typename T>
 nm_status enqueue_items_rounds(const std::vector<Item>& items, cudaStream_t s) {
     nm_status st;
-    for (const Item& it : items)
-        if ((st = enqueue_restrict<T>(it.p, it.rho, s)) != NM_OK) return st;
+    if ((st = enqueue_restrict_batch<T>(items, s)) != NM_OK) return st;
     // geometry 0: level grids; 1: doubled grids (dipole methods); 2:
     // quadrupled grids (three-level scheme)
     for (int geom = 0; geom < 3; ++geom) {
@@ -1191,9 +1252,7 @@ nm_status enqueue_items_rounds(const std::vector<Item>& items, cudaStream_t s) {
             if (e != cudaSuccess) return cuda_fail(e, "three-level term");
         }
     }
-    for (const Item& it : items)
-        if ((st = enqueue_assemble<T>(it.p, it.phi, s)) != NM_OK) return st;
-    return NM_OK;
+    return enqueue_assemble_batch<T>(items, s);
 }
 
 nm_status ensure_green(nm_plan_t p, cudaStream_t s) {

@@ -88,6 +88,14 @@ __device__ __forceinline__ void diag_axis(int N, int i, int& c, int& s) {
     c = (N / 2 + i) >> 1;
     s = (i & 1) ? 1 : -1;
 }
+// The two-point rule's weights on the nearest coarse value and its diagonal
+// neighbour, and one carried value (the rule plus the level's hole term).
+template <typename T> __device__ __forceinline__ T diag_mix(T near, T diag) {
+    return T(0.75) * near + T(0.25) * diag;
+}
+template <typename T> __device__ __forceinline__ T carry_value(T near, T diag, T hole) {
+    return diag_mix<T>(near, diag) + hole;
+}
 // The two-point rule at level-n cell (z, y, x) from a level-(n-1) field
 // stored from `o` on, `E` per axis.
 template <typename T>
@@ -98,7 +106,7 @@ __device__ __forceinline__ T diag_value(const T* src, int o, int E, int N, int z
     diag_axis(N, x, cx, sx);
     const T near = src[((size_t)(cz - o) * E + (cy - o)) * E + (cx - o)];
     const T diag = src[((size_t)(cz + sz - o) * E + (cy + sy - o)) * E + (cx + sx - o)];
-    return T(0.75) * near + T(0.25) * diag;
+    return diag_mix<T>(near, diag);
 }
 
 // One step of the carried interpolation on cells i = i0, i0 + stride, ...
@@ -113,7 +121,7 @@ __device__ __forceinline__ void carry_body(const CarryArgs<T>& a, size_t i0, siz
         const int x = (int)(i % nc) + o, y = (int)((i / nc) % nc) + o, z = (int)(i / ((size_t)nc * nc)) + o;
         const int ho = a.hole_origin, hE = a.hole_extent;
         const T h = a.hole[((size_t)(z - ho) * hE + (y - ho)) * hE + (x - ho)];
-        a.out[i] = diag_value<T>(a.prev, a.prev_origin, a.prev_extent, N, z, y, x) + h;
+        a.out[i] = diag_value<T>(a.prev, a.prev_origin, a.prev_extent, N, z, y, x) + h;   // carry_value
     }
 }
 

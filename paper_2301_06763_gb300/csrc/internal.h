@@ -135,12 +135,42 @@ template <typename T> struct CarryArgs {
 };
 template <typename T>
 cudaError_t run_carry(const CarryArgs<T>& a, cudaStream_t s);
+// The restriction and carried-interpolation chains of up to kTreeMeshes
+// meshes per launch (chains.cu).  A mesh's restriction job: rho holds its L
+// levels of N^3 densities (level m at rho + m N^3), restr receives restr_m,
+// m = 0 .. L-2, at restr + m N^3/8.  Meshes with N < 16 or unaligned buffers,
+// and the levels beyond a tile's depth, take the per-level kernel.
+constexpr int kTreeMeshes = 32;
+template <typename TIN> struct RestrictMesh {
+    const TIN* rho;
+    TIN* restr;
+    int N, L;
+};
+template <typename TIN>
+cudaError_t run_restrict_tree(const RestrictMesh<TIN>* meshes, int n, cudaStream_t s);
+// A mesh's carried interpolation: level k's hole potential at hole + k
+// hole_stride, stored from level index hole_origin on with hole_extent cells
+// per axis (k = 0 .. L-2); out + (n-1) (N/2+2)^3 receives S_n, n = 1 .. L-2.
+template <typename T> struct CarryMesh {
+    const T* hole;
+    size_t hole_stride;
+    int hole_origin, hole_extent;
+    T* out;
+    int N, L;
+};
+template <typename T>
+cudaError_t run_carry_tree(const CarryMesh<T>* meshes, int n, cudaStream_t s);
 // run_assemble after the carry chain when interp is NM_INTERP_DIAGONAL
 // (carry: (L-2) (N/2+2)^3 values of scratch).
 template <typename T>
 cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStream_t s);
 template <typename T>
 cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s);
+// The assemblies of n meshes, up to kAsmMeshes per launch (meshes with
+// N < 16 take run_assemble).
+constexpr int kAsmMeshes = 16;
+template <typename T>
+cudaError_t run_assemble_batch(const AssembleArgs<T>* meshes, int n, cudaStream_t s);
 
 // Three-level dipole scheme (dipole3.cu): out (N^3) = mean of each 4^3 block
 // of in ((4N)^3); and Eq. B.6, out (N^3, level n centres) = scale * sum over

@@ -1,4 +1,7 @@
 // support.cu -- restriction, Green spectrum and final assembly kernels.
+#include <mutex>
+#include <vector>
+
 #include "../../include/nm.h"
 #include "internal.h"
 #include "dfloat.cuh"
@@ -358,6 +361,73 @@ cudaError_t run_assemble(const AssembleArgs<T>& a, cudaStream_t s) {
 template cudaError_t run_assemble<float>(const AssembleArgs<float>&, cudaStream_t);
 template cudaError_t run_assemble<double>(const AssembleArgs<double>&, cudaStream_t);
 template cudaError_t run_assemble<df>(const AssembleArgs<df>&, cudaStream_t);
+
+// Several meshes' assemblies in one launch: CTAs [first[i], first[i+1]) walk
+// the rows of mesh i as k_assemble_rows does (N >= 16).
+template <typename T> struct AssembleBatchArgs {
+    AssembleArgs<T> mesh[kAsmMeshes];
+    int first[kAsmMeshes + 1];
+    int lgN[kAsmMeshes];
+    int nmesh;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble_rows_batch(const __grid_constant__ AssembleBatchArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_rows[];
+    int mi = 0;
+    while (mi + 1 < a.nmesh && (int)blockIdx.x >= a.first[mi + 1]) ++mi;
+    const int lgN = a.lgN[mi];
+    const int rows_cta = 256 / ((1 << lgN) >> 2);
+    const int b = (int)blockIdx.x - a.first[mi], nb = a.first[mi + 1] - a.first[mi];
+    assemble_rows_body<T>(a.mesh[mi], lgN, (size_t)b * rows_cta, nb, smem_rows);
+}
+
+template <typename T>
+cudaError_t run_assemble_batch(const AssembleArgs<T>* meshes, int n, cudaStream_t s) {
+    std::vector<int> rows_path;
+    for (int i = 0; i < n; ++i) {
+        if (meshes[i].N >= 16) {
+            rows_path.push_back(i);
+        } else {
+            cudaError_t e = run_assemble<T>(meshes[i], s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    for (size_t b = 0; b < rows_path.size(); b += kAsmMeshes) {
+        const size_t e_ = b + kAsmMeshes < rows_path.size() ? b + kAsmMeshes : rows_path.size();
+        static AssembleBatchArgs<T> args;   // host staging of the (large) parameter block
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lk(mu);
+        args = AssembleBatchArgs<T>{};
+        int grid = 0, levels = 0;
+        size_t smem = 0;
+        args.nmesh = (int)(e_ - b);
+        for (size_t i = b; i < e_; ++i) {
+            const AssembleArgs<T>& m = meshes[rows_path[i]];
+            const int team = m.N / 4, rows_cta = 256 / team;
+            const size_t rows = (size_t)m.N * m.N * m.levels;
+            size_t blocks = rows / rows_cta;
+            if (blocks > 152 * 16) blocks = 152 * 16;
+            const size_t sm = (size_t)rows_cta * (m.N / 2 + 2) * sizeof(T);
+            if (sm > smem) smem = sm;
+            args.mesh[i - b] = m;
+            args.lgN[i - b] = ilog2(m.N);
+            args.first[i - b] = grid;
+            grid += (int)blocks;
+            levels += m.levels;
+        }
+        args.first[args.nmesh] = grid;
+        ProfScope ps(sizeof(T) == 4 ? "assemble_batch_f32" : "assemble_batch_f64", levels, s);
+        k_assemble_rows_batch<T><<<grid, 256, smem, s>>>(args);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+template cudaError_t run_assemble_batch<float>(const AssembleArgs<float>*, int, cudaStream_t);
+template cudaError_t run_assemble_batch<double>(const AssembleArgs<double>*, int, cudaStream_t);
+template cudaError_t run_assemble_batch<df>(const AssembleArgs<df>*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t run_assemble_interp(AssembleArgs<T> a, int interp, T* carry, cudaStream_t s) {
