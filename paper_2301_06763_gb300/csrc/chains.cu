@@ -111,6 +111,89 @@ __device__ inline void shell_tile(int s, int G, int& tz, int& ty, int& tx) {
     tz = ty = tx = 0;   // not reached for s below the shell count
 }
 
+// One tile of restr_k (edge T, a compile-time constant so that every index
+// is shifts and masks) and its images on the coarser levels down to mmin.
+template <typename TIN, int T>
+__device__ __forceinline__ void restrict_tile_body(const RestrictMesh<TIN>& M, int k, int tz, int ty, int tx,
+                                                   int mmin, TIN* buf0, TIN* buf1) {
+    constexpr int TH = T / 2, LGT = T == 16 ? 4 : T == 8 ? 3 : T == 4 ? 2 : 1;
+    constexpr int PAIRS = T * T * TH;
+    constexpr int PER = RestrictPer<TIN>::value;
+    const int N = M.N, h = N / 2, q = N / 4;
+    const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
+    // the tile of restr_k: cells [o, o + T)^3, children on level k+1 raw
+    const TIN* rho = M.rho + (size_t)(k + 1) * N3;
+    TIN* out = M.restr + (size_t)k * h3;
+    const int oz = tz * T, oy = ty * T, ox = tx * T;
+    // every thread's children loads are issued before any sum (up to PER
+    // output pairs per thread), so that a CTA has its input in flight at once
+#pragma unroll 1
+    for (int p0 = 0; p0 < PAIRS; p0 += PER * kRestrictThreads) {
+        TIN w[PER][4][4];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int p = p0 + u * kRestrictThreads + (int)threadIdx.x;
+            if (p < PAIRS) {
+                const int cx = 2 * (p % TH), cy = (p / TH) % T, cz = p / (TH * T);
+                const TIN* src = rho + ((size_t)(2 * (oz + cz)) * N + 2 * (oy + cy)) * N + 2 * (ox + cx);
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 2; ++dy)
+                        Load4<TIN>::load(src + ((size_t)dz * N + dy) * N, w[u][2 * dz + dy]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int p = p0 + u * kRestrictThreads + (int)threadIdx.x;
+            if (p < PAIRS) {
+                const int cx = 2 * (p % TH), cy = (p / TH) % T, cz = p / (TH * T);
+                TIN s0 = TIN(0), s1 = TIN(0);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {   // (dz, dy) = (0,0), (0,1), (1,0), (1,1)
+                    s0 += w[u][r][0] + w[u][r][1];
+                    s1 += w[u][r][2] + w[u][r][3];
+                }
+                s0 *= TIN(0.125);
+                s1 *= TIN(0.125);
+                buf0[(cz * T + cy) * T + cx] = s0;
+                buf0[(cz * T + cy) * T + cx + 1] = s1;
+                TIN* o = out + ((size_t)(oz + cz) * h + (oy + cy)) * h + ox + cx;
+                o[0] = s0;
+                o[1] = s1;
+            }
+        }
+    }
+    // images R^j(tile) on restr_{k-j}: origin (o_{j-1} + N/4) / 2
+    int sz = oz, sy = oy, sx = ox;
+#pragma unroll
+    for (int j = 1; j <= LGT; ++j) {
+        if (k - j < mmin) break;
+        __syncthreads();
+        const int S = T >> (j - 1), S2 = S / 2;
+        const TIN* src = (j & 1) ? buf0 : buf1;
+        TIN* dst = (j & 1) ? buf1 : buf0;
+        sz = (sz + q) / 2;
+        sy = (sy + q) / 2;
+        sx = (sx + q) / 2;
+        TIN* lout = M.restr + (size_t)(k - j) * h3;
+        for (int c = threadIdx.x; c < S2 * S2 * S2; c += kRestrictThreads) {
+            const int x = c % S2, y = (c / S2) % S2, z = c / (S2 * S2);
+            TIN s0 = TIN(0);
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const TIN* r = src + ((2 * z + dz) * S + (2 * y + dy)) * S + 2 * x;
+                    s0 += r[0] + r[1];
+                }
+            s0 *= TIN(0.125);
+            dst[(z * S2 + y) * S2 + x] = s0;
+            lout[((size_t)(sz + z) * h + (sy + y)) * h + (sx + x)] = s0;
+        }
+    }
+}
+
 template <typename TIN>
 __global__ void __launch_bounds__(kRestrictThreads, 2) k_restrict_tree(const __grid_constant__ RestrictTreeArgs<TIN> a) {
     constexpr int T_MAX = kRestrictTile;
@@ -119,7 +202,7 @@ __global__ void __launch_bounds__(kRestrictThreads, 2) k_restrict_tree(const __g
     int mi = 0;
     while (mi + 1 < a.nmesh && (int)blockIdx.x >= a.first[mi + 1]) ++mi;
     const RestrictMesh<TIN>& M = a.mesh[mi];
-    const int N = M.N, L = M.L, h = N / 2, q = N / 4;
+    const int N = M.N, L = M.L, h = N / 2;
     const int T = restrict_tile(N), lgT = __ffs(T) - 1, G = h / T;
     int mmin = L - 2 - lgT;
     if (mmin < 0) mmin = 0;
@@ -136,86 +219,11 @@ __global__ void __launch_bounds__(kRestrictThreads, 2) k_restrict_tree(const __g
         k = L - 3 - t / S;
         shell_tile(t % S, G, tz, ty, tx);   // k >= mmin: the launch holds no shell below
     }
-    const size_t N3 = (size_t)N * N * N, h3 = N3 / 8;
-    // the tile of restr_k: cells [o, o + T)^3, children on level k+1 raw
-    const TIN* rho = M.rho + (size_t)(k + 1) * N3;
-    {
-        TIN* out = M.restr + (size_t)k * h3;
-        const int oz = tz * T, oy = ty * T, ox = tx * T;
-        const int TH = T / 2;
-        // every thread's children loads are issued before any sum (up to
-        // kRestrictPer output pairs per thread), so that a CTA has its whole
-        // (2T)^3 input in flight at once
-        const int pairs = T * T * TH;
-        constexpr int kRestrictPer = RestrictPer<TIN>::value;
-        for (int p0 = 0; p0 < pairs; p0 += kRestrictPer * (int)blockDim.x) {
-            TIN w[kRestrictPer][4][4];
-#pragma unroll
-            for (int u = 0; u < kRestrictPer; ++u) {
-                const int p = p0 + u * (int)blockDim.x + (int)threadIdx.x;
-                if (p < pairs) {
-                    const int cx = 2 * (p % TH), cy = (p / TH) % T, cz = p / (TH * T);
-                    const int az = oz + cz, ay = oy + cy, ax = ox + cx;
-#pragma unroll
-                    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                        for (int dy = 0; dy < 2; ++dy)
-                            Load4<TIN>::load(rho + ((size_t)(2 * az + dz) * N + (2 * ay + dy)) * N + 2 * ax,
-                                             w[u][2 * dz + dy]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kRestrictPer; ++u) {
-                const int p = p0 + u * (int)blockDim.x + (int)threadIdx.x;
-                if (p < pairs) {
-                    const int cx = 2 * (p % TH), cy = (p / TH) % T, cz = p / (TH * T);
-                    const int az = oz + cz, ay = oy + cy, ax = ox + cx;
-                    TIN s0 = TIN(0), s1 = TIN(0);
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {   // (dz, dy) = (0,0), (0,1), (1,0), (1,1)
-                        s0 += w[u][r][0] + w[u][r][1];
-                        s1 += w[u][r][2] + w[u][r][3];
-                    }
-                    s0 *= TIN(0.125);
-                    s1 *= TIN(0.125);
-                    buf0[(cz * T + cy) * T + cx] = s0;
-                    buf0[(cz * T + cy) * T + cx + 1] = s1;
-                    TIN* o = out + ((size_t)az * h + ay) * h + ax;
-                    o[0] = s0;
-                    o[1] = s1;
-                }
-            }
-        }
-        // images R^j(tile) on restr_{k-j}: origin (o_{j-1} + N/4) / 2
-        int sz_ = oz, sy_ = oy, sx_ = ox, S = T;
-        TIN* src = buf0;
-        TIN* dst = buf1;
-        for (int j = 1; j <= lgT && k - j >= mmin; ++j) {
-            __syncthreads();
-            const int S2 = S / 2;
-            sz_ = (sz_ + q) / 2;
-            sy_ = (sy_ + q) / 2;
-            sx_ = (sx_ + q) / 2;
-            TIN* lout = M.restr + (size_t)(k - j) * h3;
-            for (int c = threadIdx.x; c < S2 * S2 * S2; c += blockDim.x) {
-                const int x = c % S2, y = (c / S2) % S2, z = c / (S2 * S2);
-                TIN s0 = TIN(0);
-#pragma unroll
-                for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                    for (int dy = 0; dy < 2; ++dy) {
-                        const TIN* r = src + ((2 * z + dz) * S + (2 * y + dy)) * S + 2 * x;
-                        s0 += r[0] + r[1];
-                    }
-                s0 *= TIN(0.125);
-                dst[(z * S2 + y) * S2 + x] = s0;
-                lout[((size_t)(sz_ + z) * h + (sy_ + y)) * h + (sx_ + x)] = s0;
-            }
-            TIN* tmp = src;
-            src = dst;
-            dst = tmp;
-            S = S2;
-        }
+    switch (T) {
+        case 16: restrict_tile_body<TIN, 16>(M, k, tz, ty, tx, mmin, buf0, buf1); break;
+        case 8: restrict_tile_body<TIN, 8>(M, k, tz, ty, tx, mmin, buf0, buf1); break;
+        case 4: restrict_tile_body<TIN, 4>(M, k, tz, ty, tx, mmin, buf0, buf1); break;
+        default: restrict_tile_body<TIN, 2>(M, k, tz, ty, tx, mmin, buf0, buf1); break;
     }
 }
 
@@ -334,24 +342,44 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_tree(const __grid_const
         const int pz = k >= 2 ? lo[k - 1][0] : 0, py = k >= 2 ? lo[k - 1][1] : 0, px = k >= 2 ? lo[k - 1][2] : 0;
         const int pey = k >= 2 ? hi[k - 1][1] - lo[k - 1][1] + 1 : 0;
         const int pex = k >= 2 ? hi[k - 1][2] - lo[k - 1][2] + 1 : 0;
-        for (int c = threadIdx.x; c < ez * ey * ex; c += blockDim.x) {
-            const int x = lo[k][2] + c % ex, y = lo[k][1] + (c / ex) % ey, z = lo[k][0] + c / (ex * ey);
+        // cell c = threadIdx.x + i blockDim.x of the box, its (z, y, x)
+        // advanced by the fixed step instead of divided out per cell
+        const int cells = ez * ey * ex;
+        const int stx = kCarryThreads % ex, sty = (kCarryThreads / ex) % ey, stz = kCarryThreads / (ex * ey);
+        int bx = (int)threadIdx.x % ex, by = ((int)threadIdx.x / ex) % ey, bz = (int)threadIdx.x / (ex * ey);
+        const T* __restrict__ hk = hole;
+        T* __restrict__ outk = M.out + (size_t)(n - 1) * nc3;
+        for (int c = threadIdx.x; c < cells; c += kCarryThreads) {
+            const int x = lo[k][2] + bx, y = lo[k][1] + by, z = lo[k][0] + bz;
             int cz, sz, cy, sy, cx, sx;
             diag_axis(N, z, cz, sz);
             diag_axis(N, y, cy, sy);
             diag_axis(N, x, cx, sx);
             T near, diag;
             if (k == 1) {
-                near = prev_g[((size_t)(cz - ho) * hE + (cy - ho)) * hE + (cx - ho)];
-                diag = prev_g[((size_t)(cz + sz - ho) * hE + (cy + sy - ho)) * hE + (cx + sx - ho)];
+                near = prev_g[((cz - ho) * hE + (cy - ho)) * hE + (cx - ho)];
+                diag = prev_g[((cz + sz - ho) * hE + (cy + sy - ho)) * hE + (cx + sx - ho)];
             } else {
                 near = prev_s[((cz - pz) * pey + (cy - py)) * pex + (cx - px)];
                 diag = prev_s[((cz + sz - pz) * pey + (cy + sy - py)) * pex + (cx + sx - px)];
             }
-            const T hv = hole[((size_t)(z - ho) * hE + (y - ho)) * hE + (x - ho)];
+            const T hv = hk[((z - ho) * hE + (y - ho)) * hE + (x - ho)];
             const T v = carry_value(near, diag, hv);
             if (k < n) cur[c] = v;
-            else M.out[(size_t)(n - 1) * nc3 + ((size_t)(z - o) * nc + (y - o)) * nc + (x - o)] = v;
+            else outk[((z - o) * nc + (y - o)) * nc + (x - o)] = v;
+            bx += stx;
+            int up = 0;
+            if (bx >= ex) {
+                bx -= ex;
+                up = 1;
+            }
+            by += sty + up;
+            up = 0;
+            if (by >= ey) {
+                by -= ey;
+                up = 1;
+            }
+            bz += stz + up;
         }
         __syncthreads();
     }
