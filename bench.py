@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the oracle CPU timing (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--mode", choices=["solve", "batch", "serve", "accel", "table"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "batch", "serve", "accel", "table", "fp32"], default="solve",
+                    help="fp32: FP32 solves of the --levels x --N mesh alone, library default "
+                         "schedule (the small cases that ncu captures run)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window per rate (requests = rate x seconds, at most 2000)")
@@ -788,6 +790,34 @@ def accel_mode(args):
                       "peak_kind": kind, "data": "synthetic", "dtype": "f64", **a}))
 
 
+# ----------------------------------------------------------------------------- fp32 mode
+def fp32_mode(args):
+    """--warmup + --steps FP32 solves of the --levels x --N benchmark mesh with
+    the library's default schedule and nothing else on the GPU: the small,
+    short cases that ncu captures run.  One JSON line."""
+    import torch
+    from paper_2301_06763_gb300 import build
+    build.build()
+    from paper_2301_06763_gb300 import nm, workloads as wl
+    w = wl.config_contrast(levels=args.levels, N=args.N)
+    rho = torch.from_numpy(w.rho()).to("cuda", torch.float32)
+    phi = torch.empty(rho.shape, dtype=torch.float64, device="cuda")
+    with nm.Plan(args.levels, args.N, w.dx0, precision="fp32") as p:
+        for _ in range(args.warmup):
+            p.potential(rho, phi)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            p.potential(rho, phi)
+        b.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "fp32", "workload": w.name, "levels": args.levels, "N": args.N,
+                          "schedule": p.schedule(), "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_solve": a.elapsed_time(b) / max(args.steps, 1),
+                          "note": "same rho every solve (inputs partly in L2): for profiling, not a bench value"}))
+
+
 # ----------------------------------------------------------------------------- serve mode
 def serve_mode(args):
     """Poisson request streams at several rates through the continuous-batching
@@ -1006,6 +1036,8 @@ def main():
         accel_mode(args)
     elif args.mode == "table":
         table_mode(args)
+    elif args.mode == "fp32":
+        fp32_mode(args)
     else:
         ours(args)
 

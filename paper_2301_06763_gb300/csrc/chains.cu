@@ -349,8 +349,10 @@ __global__ void __launch_bounds__(kCarryThreads) k_carry_tree(const __grid_const
         int bx = (int)threadIdx.x % ex, by = ((int)threadIdx.x / ex) % ey, bz = (int)threadIdx.x / (ex * ey);
         const T* __restrict__ hk = hole;
         T* __restrict__ outk = M.out + (size_t)(n - 1) * nc3;
+        const int lz = lo[k][0], ly = lo[k][1], lx = lo[k][2];
+#pragma unroll 4
         for (int c = threadIdx.x; c < cells; c += kCarryThreads) {
-            const int x = lo[k][2] + bx, y = lo[k][1] + by, z = lo[k][0] + bz;
+            const int x = lx + bx, y = ly + by, z = lz + bz;
             int cz, sz, cy, sy, cx, sx;
             diag_axis(N, z, cz, sz);
             diag_axis(N, y, cy, sy);
