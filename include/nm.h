@@ -237,7 +237,10 @@ typedef struct {
     int pipeline;/* z-seam pass: 0 = one tile per CTA; 1 = persistent CTAs fed
                     by a two-stage TMA (cp.async.bulk.tensor) pipeline;
                     2 = two columns per thread on paired FP32 instructions
-                    (FP32 plans, radix 16, P = 2N >= 64, fuse 0)              */
+                    (FP32 plans, radix 16, P = 2N >= 64, fuse 0);
+                    3 = the same as persistent CTAs, each fetching its next
+                    tile's columns while it transforms the current one
+                    (FP32 plans, radix 16, P = 2N = 256, tile 0, fuse 0)      */
     int fuse;    /* 1 = x and y passes fused per z-slab through a thread-block
                     cluster (distributed shared memory), 3 launches per level
                     group instead of 5; needs radix 16; 0 = five passes;
@@ -256,7 +259,7 @@ nm_status nm_get_schedule(nm_plan_t plan, nm_schedule* out);
 nm_status nm_set_schedule(nm_plan_t plan, const nm_schedule* sched);
 
 /* Autotuner: times every candidate schedule (group in {1, 2, all}, radix in
- * {16, 8}, tile in {0, 1}, pipeline in {0, 1, 2}, fuse in {0, 1, 2}, where valid) with CUDA events over `reps` solves of the
+ * {16, 8}, tile in {0, 1}, pipeline in {0, 1, 2, 3}, fuse in {0, 1, 2, 3}, where valid) with CUDA events over `reps` solves of the
  * caller's rho into phi (phi is overwritten), on `stream`, keeps the fastest
  * on the plan and records it in a process-wide table keyed by (device name,
  * N, levels, precision, method) that later plans of the same key start from.

@@ -520,9 +520,13 @@ bool sched_valid(nm_plan_t p, const nm_schedule& sc) {
     if (sc.radix != 8 && sc.radix != 16) return false;
     if (sc.radix == 16 && p->P < 16) return false;
     if (p->dfx && sc.radix != 16) return false;
-    if (sc.pipeline < 0 || sc.pipeline > 2) return false;
+    if (sc.pipeline < 0 || sc.pipeline > 3) return false;
     // two columns per thread: FP32 level grids, 16 values per thread, P >= 64
     if (sc.pipeline == 2 && (!p->fp32 || p->dfx || sc.radix != 16 || p->P < 64 || sc.fuse)) return false;
+    // the same, persistent with the next tile's columns prefetched: P = 256,
+    // narrow tiles
+    if (sc.pipeline == 3 && (!p->fp32 || p->dfx || sc.radix != 16 || p->P != 256 || sc.fuse || sc.tile))
+        return false;
     if (sc.fuse < 0 || sc.fuse > 3) return false;
     if (sc.fuse && sc.radix != 16) return false;
     // three-pass form (fused y/z/y per kx plane): FP32 level grids of the
@@ -920,7 +924,8 @@ cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, int geom, const nm_
         }
         const bool e16 = dbl || (sc.radix == 16 && P >= 16);
         const int flags = (sc.fuse != 2 && sc.tile ? CONV_WIDE : 0) | (sc.pipeline == 1 ? CONV_TMA : 0) |
-                          (sc.pipeline == 2 ? CONV_PAIRED : 0) | (sc.fuse == 1 ? CONV_FUSED : 0);
+                          (sc.pipeline >= 2 ? CONV_PAIRED : 0) | (sc.pipeline == 3 ? CONV_ZPERSIST : 0) |
+                          (sc.fuse == 1 ? CONV_FUSED : 0);
         if constexpr (sizeof(T) == 4) {
             return e16 ? run_conv_f32_e16(pairs, n, P, dbl, flags, spec, tw, s)
                        : run_conv_f32_e8(pairs, n, P, dbl, flags, spec, tw, s);
@@ -1260,7 +1265,7 @@ nm_status ensure_green(nm_plan_t p, cudaStream_t s) {
         nm_status st = nm_green(p, (void*)s);
         if (st != NM_OK) return st;
     }
-    if (p->sched.pipeline == 2 && !p->spec->d32x) {
+    if (p->sched.pipeline >= 2 && !p->spec->d32x) {
         nm_status st = build_unfolded(p->spec, s);
         if (st != NM_OK) return st;
     }
@@ -1478,8 +1483,8 @@ nm_status nm_set_schedule(nm_plan_t p, const nm_schedule* sc) {
     if (!p || !sc) return fail(NM_EINVAL, "nm_set_schedule: null argument");
     if (!sched_valid(p, *sc))
         return fail(NM_EINVAL,
-                    "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile 0 or 1, pipeline 0, 1 "
-                    "or 2 (2: FP32, radix 16, P >= 64, not fused), fuse 0, 1 or 2 (2: FP32 original method, "
+                    "nm_set_schedule: group must be in [1, %d], radix 16 (P >= 16) or 8, tile 0 or 1, pipeline 0, 1, "
+                    "2 (FP32, radix 16, P >= 64, not fused) or 3 (the same with P = 256, tile 0), fuse 0, 1 or 2 (2: FP32 original method, "
                     "radix 16, pipeline 0, 64 <= P <= 512, tile 1 only for P = 128 or 256) or 3 (FP32 original method, "
                     "radix 16, pipeline 0, tile 0, 64 <= P <= 512)",
                     p->npairs);
@@ -1500,7 +1505,7 @@ nm_status nm_autotune(nm_plan_t p, const void* rho, double* phi, int reps, void*
     for (int g : groups)
         for (int radix : {16, 8})
             for (int tile : {0, 1})
-                for (int pipe : {2, 1, 0})
+                for (int pipe : {3, 2, 1, 0})
                     for (int fuse : {3, 2, 1, 0}) {
                         nm_schedule c{g, radix, tile, pipe, fuse};
                         if (!sched_valid(p, c)) continue;

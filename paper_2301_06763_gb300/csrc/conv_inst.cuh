@@ -188,7 +188,11 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
         ProfScope ps(nm_, np, s);
         bool done = false;
         if constexpr (GM == 0 && E == 16 && P >= 64 && sizeof(T) == 4 && !is_df<T>::value) {
-            if (flags & CONV_PAIRED) {
+            if ((flags & CONV_ZPERSIST) && P == 256 && TX == 16) {
+                cudaError_t e = run_zseam_persist_f32(a, np, P, s);
+                if (e != cudaSuccess) return e;
+                done = true;
+            } else if (flags & CONV_PAIRED) {
                 cudaError_t e = run_zseam_paired_f32(a, np, P, TX, s);
                 if (e != cudaSuccess) return e;
                 done = true;
