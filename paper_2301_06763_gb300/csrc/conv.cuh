@@ -146,7 +146,6 @@ __device__ __forceinline__ void xfwd_body(const PairDesc<T>& d, const cpx<T>* tw
     constexpr int LINES = 256 / TPL;
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
-    load_twiddles<P, E, true>(sm_tw, tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int row0 = tile * LINES;
     const int row = row0 + line;
@@ -200,6 +199,7 @@ __device__ __forceinline__ void xfwd_body(const PairDesc<T>& d, const cpx<T>* tw
             }
         }
     }
+    load_twiddles<P, E, true>(sm_tw, tw);   // after the density loads are out
     __syncthreads();
     fft_line<T, P, E, false, G::LIVE, false, true>(v, j, sm_tw,
                                              LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
@@ -445,7 +445,6 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
     cpx<T>* sm_tile = sm_tw + P;
     const PairDesc<T>& d = a.pair[blockIdx.z];
     if (d.half && blockIdx.x * TX > P / 2) return;   // the column tile is above kx = P/2 (whole CTA)
-    load_twiddles<P, E>(sm_tw, a.tw);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
     __builtin_assume(j < P / E);
     const int z = (INV ? 0 : G::OFF) + blockIdx.y;
@@ -457,6 +456,7 @@ __global__ void __launch_bounds__(TX * P / E) k_ypass(const __grid_constant__ Co
         if (INV || G::live(r)) v[r] = slab[(size_t)(j + r * (P / E)) * P + x];
         else v[r] = {T(0), T(0)};
     }
+    load_twiddles<P, E>(sm_tw, a.tw);   // after the column loads are out
     __syncthreads();
     fft_line<T, P, E, INV, INV ? 0xFFFFu : G::LIVE, false>(v, j, sm_tw, LineView<T, TX, false>{sm_tile + l});
 #pragma unroll
@@ -485,7 +485,6 @@ __device__ __forceinline__ void zseam_body(const PairDesc<T>& d, const T* spec, 
     constexpr int H = P / 2 + 1;
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_tile = sm_tw + P;
-    load_twiddles<P, E, true>(sm_tw, tw);
     const int l = threadIdx.x % TX, j = threadIdx.x / TX;
     // blockDim.x = TX P/E: lets the compiler see which outputs of the last
     // pass the window keeps, and drop the rest
@@ -498,6 +497,7 @@ __device__ __forceinline__ void zseam_body(const PairDesc<T>& d, const T* spec, 
         if (G::live(r)) v[r] = col[(size_t)(j + r * (P / E)) * P * P];
         else v[r] = {T(0), T(0)};
     }
+    load_twiddles<P, E, true>(sm_tw, tw);   // after the column loads are out
     __syncthreads();
     const LineView<T, TX, false> view{sm_tile + l};
     fft_line<T, P, E, false, G::LIVE, true, true>(v, j, sm_tw, view);
@@ -562,6 +562,22 @@ __global__ void __launch_bounds__(TX / 2 * P / E, Zseam2MinBlocks<TX / 2 * P / E
     if (d.half && blockIdx.x * TX > P / 2) return;   // above kx = P/2 (whole CTA)
     const int y = blockIdx.y;
     const int fy = y <= P / 2 ? y : P - y;
+    const int l = threadIdx.x % TX2, j = threadIdx.x / TX2;
+    __builtin_assume(j < P / E);
+    const int x = blockIdx.x * TX + 2 * l;
+    cpx<float>* col = d.work + (size_t)y * P + x;      // columns x, x + 1: element z at col[z * P * P]
+    // the column loads go out first: the twiddle staging below waits on its
+    // own (L2) loads, and would otherwise hold them back
+    cpx<f2> v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        if (G::live(r)) {
+            const float4 q = *reinterpret_cast<const float4*>(col + (size_t)(j + r * (P / E)) * P * P);
+            v[r] = {f2(q.x, q.z), f2(q.y, q.w)};
+        } else {
+            v[r] = {f2(0), f2(0)};
+        }
+    }
     {
         const float* sp = a.spec + (size_t)fy * P + blockIdx.x * TX;
         for (int i = threadIdx.x; i < H * (TX / 4); i += blockDim.x) {
@@ -573,20 +589,6 @@ __global__ void __launch_bounds__(TX / 2 * P / E, Zseam2MinBlocks<TX / 2 * P / E
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const cpx<float> w = a.tw[i];
         sm_tw[i] = {f2(w.re, w.re), f2(w.im, w.im)};
-    }
-    const int l = threadIdx.x % TX2, j = threadIdx.x / TX2;
-    __builtin_assume(j < P / E);
-    const int x = blockIdx.x * TX + 2 * l;
-    cpx<float>* col = d.work + (size_t)y * P + x;      // columns x, x + 1: element z at col[z * P * P]
-    cpx<f2> v[E];
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        if (G::live(r)) {
-            const float4 q = *reinterpret_cast<const float4*>(col + (size_t)(j + r * (P / E)) * P * P);
-            v[r] = {f2(q.x, q.z), f2(q.y, q.w)};
-        } else {
-            v[r] = {f2(0), f2(0)};
-        }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -632,7 +634,6 @@ __device__ __forceinline__ void xinv_body(const PairDesc<T>& d, const cpx<T>* tw
     constexpr int HALF = P / 2;
     cpx<T>* sm_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* sm_lines = sm_tw + P;
-    load_twiddles<P, E, true>(sm_tw, tw);
     const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
     const int row = tile * LINES + line;
     const bool valid = row < HALF * HALF;
@@ -650,6 +651,7 @@ __device__ __forceinline__ void xinv_body(const PairDesc<T>& d, const cpx<T>* tw
         if (up) w.im = -w.im;
         v[r] = w;
     }
+    load_twiddles<P, E, true>(sm_tw, tw);   // after the row loads are out
     __syncthreads();
     fft_line<T, P, E, true, 0xFFFFu, false, true>(v, j, sm_tw,
                                             LineView<T, 1, true, Log2E<E>::value>{sm_lines + line * (P + P / E)});
