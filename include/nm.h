@@ -234,7 +234,10 @@ typedef struct {
                     1 = 256-byte rows; with fuse 2, the CTAs per kx plane:
                     0 = the default split for P, 1 = the alternative one
                     (P = 128: 4 instead of 2; P = 256: 2 instead of 4)        */
-    int pipeline;/* z-seam pass: 0 = one tile per CTA; 1 = persistent CTAs fed
+    int pipeline;/* z-seam pass: 0 = one tile per CTA, one column per thread
+                    (the default; FP32 level grids with P = 2N >= 64 stage
+                    the CTA's spectrum rows in shared memory by cp.async
+                    while the column loads are in flight); 1 = persistent CTAs fed
                     by a two-stage TMA (cp.async.bulk.tensor) pipeline;
                     2 = two columns per thread on paired FP32 instructions
                     (FP32 plans, radix 16, P = 2N >= 64, fuse 0);

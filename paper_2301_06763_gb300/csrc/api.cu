@@ -708,10 +708,10 @@ nm_status nm_plan_ex(const nm_options* opt, nm_plan_t* out) {
     p->sched.group = default_group(work_buf_bytes(p), p->npairs);
     p->sched.radix = p->P >= 16 ? 16 : 8;
     p->sched.tile = 0;
-    // FP32 at P >= 256: the z-seam with two columns per thread (measured
-    // faster on the 6 x 128^3 mesh); smaller FFT sizes keep one column per
-    // thread unless the autotuner finds otherwise
-    p->sched.pipeline = (p->fp32 && !p->dfx && p->P >= 256) ? 2 : 0;
+    // one column per thread, one tile per CTA; in FP32 with P >= 64 the
+    // CTA's spectrum rows are staged in shared memory (measured faster than
+    // the paired z-seam on the 6 x 128^3 mesh: 197 against 209 us)
+    p->sched.pipeline = 0;
     p->sched.fuse = 0;
     nm_schedule tuned;
     if (tune_lookup(p, &tuned) && sched_valid(p, tuned)) p->sched = tuned;
@@ -923,9 +923,12 @@ cudaError_t run_conv(const PairDesc<T>* pairs, int n, int P, int geom, const nm_
                 return run_conv_f32_yzy(pairs, n, P, sc.tile, spec, tw, s);
         }
         const bool e16 = dbl || (sc.radix == 16 && P >= 16);
+        // FP32 level grids with the one-column z-seam stage their spectrum
+        // rows (the plan built the unfolded float spectrum, ensure_green)
+        const bool sspec = sizeof(T) == 4 && geom == 0 && sc.pipeline == 0 && P >= 64;
         const int flags = (sc.fuse != 2 && sc.tile ? CONV_WIDE : 0) | (sc.pipeline == 1 ? CONV_TMA : 0) |
                           (sc.pipeline >= 2 ? CONV_PAIRED : 0) | (sc.pipeline == 3 ? CONV_ZPERSIST : 0) |
-                          (sc.fuse == 1 ? CONV_FUSED : 0);
+                          (sc.fuse == 1 ? CONV_FUSED : 0) | (sspec ? CONV_SSPEC : 0);
         if constexpr (sizeof(T) == 4) {
             return e16 ? run_conv_f32_e16(pairs, n, P, dbl, flags, spec, tw, s)
                        : run_conv_f32_e8(pairs, n, P, dbl, flags, spec, tw, s);
@@ -1265,7 +1268,10 @@ nm_status ensure_green(nm_plan_t p, cudaStream_t s) {
         nm_status st = nm_green(p, (void*)s);
         if (st != NM_OK) return st;
     }
-    if (p->sched.pipeline >= 2 && !p->spec->d32x) {
+    // the paired z-seam and the one-column FP32 z-seam read the float spectrum
+    // unfolded along kx
+    const bool unfolded = p->sched.pipeline >= 2 || (p->sched.pipeline == 0 && p->fp32 && !p->dfx && p->P >= 64);
+    if (unfolded && !p->spec->d32x) {
         nm_status st = build_unfolded(p->spec, s);
         if (st != NM_OK) return st;
     }

@@ -612,6 +612,67 @@ __global__ void __launch_bounds__(TX / 2 * P / E, Zseam2MinBlocks<TX / 2 * P / E
     }
 }
 
+// Pass 3 in FP32, one column per thread, with the CTA's spectrum rows
+// staged in shared memory: the arithmetic of zseam_body (level grids), but
+// the spectrum comes from the float rows unfolded along kx (a.spec as for
+// k_zseam2), so that the TX columns of every fz row are one aligned 4 TX-byte
+// run; its asynchronous 16-byte copies go out right after the column loads
+// and land while the forward transform runs, instead of 16 dependent L2
+// loads per thread between the two transforms.
+template <int P, int E, int TX>
+__global__ void __launch_bounds__(TX * P / E, (ZseamMinBlocks<float, TX * P / E>::value))
+    k_zseam_s(const __grid_constant__ ConvArgs<float> a) {
+    using G = Geo<P, E, 0>;
+    constexpr int H = P / 2 + 1;
+    static_assert(TX % 4 == 0, "16-byte spectrum runs");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float>* sm_tw = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<float>* sm_tile = sm_tw + P;
+    float* sm_sp = reinterpret_cast<float*>(sm_tile + TX * P);      // [H][TX]
+    const PairDesc<float>& d = a.pair[blockIdx.z];
+    if (d.half && blockIdx.x * TX > P / 2) return;   // above kx = P/2 (whole CTA)
+    const int y = blockIdx.y;
+    const int fy = y <= P / 2 ? y : P - y;
+    const int l = threadIdx.x % TX, j = threadIdx.x / TX;
+    __builtin_assume(j < P / E);
+    const int x = blockIdx.x * TX + l;
+    cpx<float>* col = d.work + (size_t)y * P + x;      // element z at col[z * P * P]
+    cpx<float> v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        if (G::live(r)) v[r] = col[(size_t)(j + r * (P / E)) * P * P];
+        else v[r] = {0.f, 0.f};
+    }
+    {
+        const float* sp = a.spec + (size_t)fy * P + blockIdx.x * TX;
+        for (int i = threadIdx.x; i < H * (TX / 4); i += blockDim.x) {
+            const int fz = i / (TX / 4), c = i % (TX / 4);
+            cp_async16(sm_sp + fz * TX + 4 * c, sp + (size_t)fz * H * P + 4 * c);
+        }
+        cp_async_commit();
+    }
+    load_twiddles<P, E, true>(sm_tw, a.tw);
+    cp_async_wait_all();
+    __syncthreads();
+    const LineView<float, TX, false> view{sm_tile + l};
+    fft_line<float, P, E, false, G::LIVE, true, true>(v, j, sm_tw, view);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const int kz = out_index<P, E>(j, s);
+        const int fz = kz <= P / 2 ? kz : P - kz;
+        const float g = sm_sp[fz * TX + l];
+        v[s].re *= g;
+        v[s].im *= g;
+    }
+    seam_permute<float, P, E>(v);
+    fft_line<float, P, E, true, 0xFFFFu, false, true>(v, j, sm_tw, view);
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+        const int e = out_index<P, E>(j, s);
+        if (e < G::NOUT) col[(size_t)e * P * P] = v[s];
+    }
+}
+
 // ---------------------------------------------------------------- pass 5
 template <typename T, int P>
 __device__ __forceinline__ void store_out(const DstField& f, int z, int y, int x, T val) {

@@ -39,6 +39,49 @@ static cudaError_t zseam2_p(const ConvArgs<float>& a, int np, int P, cudaStream_
     }
 }
 
+template <int P, int TX>
+static cudaError_t launch_zseam_s(const ConvArgs<float>& a, int np, cudaStream_t s) {
+    constexpr int E = 16, NT = TX * P / E, H = P / 2 + 1;
+    const size_t smem = (size_t)P * sizeof(cpx<float>) + (size_t)TX * P * sizeof(cpx<float>) +
+                        (size_t)H * TX * sizeof(float);
+    static PerDevice<cudaError_t> prep;   // the shared-memory limit, once per device
+    const cudaError_t pe = prep.get(current_device(), [&]() {
+        return cudaFuncSetAttribute(k_zseam_s<P, E, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }, cudaErrorInvalidDevice);
+    if (pe != cudaSuccess) return pe;
+    const float* specx = unfolded_spectrum(a.spec);
+    if (!specx) return cudaErrorInvalidValue;
+    static ConvArgs<float> b;   // host staging of the (large) parameter block
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    b = a;
+    b.spec = specx;
+    k_zseam_s<P, E, TX><<<dim3(P / TX, P, np), NT, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t run_zseam_staged_f32(const ConvArgs<float>& a, int np, int P, int TX, cudaStream_t s) {
+    if (TX == 16) {
+        switch (P) {
+            case 64: return launch_zseam_s<64, 16>(a, np, s);
+            case 128: return launch_zseam_s<128, 16>(a, np, s);
+            case 256: return launch_zseam_s<256, 16>(a, np, s);
+            case 512: return launch_zseam_s<512, 16>(a, np, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (TX == 32) {
+        switch (P) {
+            case 64: return launch_zseam_s<64, 32>(a, np, s);
+            case 128: return launch_zseam_s<128, 32>(a, np, s);
+            case 256: return launch_zseam_s<256, 32>(a, np, s);
+            case 512: return launch_zseam_s<512, 32>(a, np, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int P>
 static cudaError_t launch_xfwd2(const ConvArgs<float>& a, int np, cudaStream_t s) {
     constexpr int E = 16, TPL = P / E, LINES = 256 / TPL, LP = LINES / 2, N = P / 2;

@@ -149,10 +149,9 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
                        (!d.src[0].restr || ((uintptr_t)d.src[0].restr & 7) == 0) &&
                        (d.src[1].mode == SRC_NONE || (d.src[1].mode == SRC_HOLE && d.src[1].rho == d.src[0].rho));
             }
-            if (pipe && P >= 256 && sizeof(T) == 4 && !is_df<T>::value && (flags & CONV_PAIRED)) {
-                // with the paired z-seam and P >= 256, the x-forward takes two
-                // rows per thread (measured 3-9% faster there, 7% slower at
-                // P = 128)
+            if (pipe && P >= 256 && sizeof(T) == 4 && !is_df<T>::value && (flags & (CONV_PAIRED | CONV_SSPEC))) {
+                // FP32 with P >= 256: the x-forward takes two rows per thread
+                // (measured 3-9% faster there, 7% slower at P = 128)
                 if constexpr (P >= 256 && sizeof(T) == 4 && !is_df<T>::value) {
                     cudaError_t e = run_xfwd_paired_f32(a, np, P, s);
                     if (e != cudaSuccess) return e;
@@ -194,6 +193,10 @@ static cudaError_t conv_passes(const ConvArgs<T>& a, int np, int flags, cudaStre
                 done = true;
             } else if (flags & CONV_PAIRED) {
                 cudaError_t e = run_zseam_paired_f32(a, np, P, TX, s);
+                if (e != cudaSuccess) return e;
+                done = true;
+            } else if ((flags & CONV_SSPEC) && !tma) {
+                cudaError_t e = run_zseam_staged_f32(a, np, P, TX, s);
                 if (e != cudaSuccess) return e;
                 done = true;
             }

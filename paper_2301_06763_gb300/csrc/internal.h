@@ -43,12 +43,17 @@ struct ProfScope {
 // thread; sizes whose slab does not fit a cluster keep the five passes),
 // CONV_PAIRED the FP32 z-seam with two columns per thread (level grids, 16
 // values per thread, P >= 64; other cases keep the classic z-seam), with
-// CONV_ZPERSIST its persistent prefetching form (P = 256, narrow tiles).  `dbl`
-// selects the doubled-fine-grid geometry (16 values, narrow tiles only).
-// Returns the first launch error.
-enum { CONV_WIDE = 1, CONV_TMA = 2, CONV_FUSED = 4, CONV_PAIRED = 8, CONV_ZPERSIST = 16 };
+// CONV_ZPERSIST its persistent prefetching form (P = 256, narrow tiles), and
+// CONV_SSPEC the one-column FP32 z-seam with its spectrum rows staged in
+// shared memory (level grids, 16 values per thread, P >= 64; both read the
+// float spectrum unfolded along kx, which must exist).  `dbl` selects the
+// doubled-fine-grid geometry (16 values, narrow tiles only).  Returns the
+// first launch error.
+enum { CONV_WIDE = 1, CONV_TMA = 2, CONV_FUSED = 4, CONV_PAIRED = 8, CONV_ZPERSIST = 16, CONV_SSPEC = 32 };
 // k_zseam2 over np pairs of FFT size P with TX columns per CTA (16 or 32).
 cudaError_t run_zseam_paired_f32(const ConvArgs<float>& a, int np, int P, int TX, cudaStream_t s);
+// k_zseam_s over np pairs of FFT size P with TX columns per CTA (16 or 32).
+cudaError_t run_zseam_staged_f32(const ConvArgs<float>& a, int np, int P, int TX, cudaStream_t s);
 // k_zseam2p, the paired z-seam as a persistent pipeline that prefetches the
 // next tile's columns (P = 256, 16 columns per tile).
 cudaError_t run_zseam_persist_f32(const ConvArgs<float>& a, int np, int P, cudaStream_t s);
