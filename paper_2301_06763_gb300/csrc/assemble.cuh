@@ -34,6 +34,12 @@ __device__ __forceinline__ void axis_stencil(int N, int lgr, int i, int& i0, T& 
 // on the final additions.
 __device__ __forceinline__ double widen(float f) {
     const unsigned u = __float_as_uint(f);
+    const unsigned mag = u & 0x7fffffffu;
+    if (mag - 0x00800000u < 0x7f000000u) {
+        // normal numbers (exponent field 1 .. 254), the common case: the high
+        // word is sign | (e + 896) << 20 | m >> 3, the low word m << 29
+        return __hiloint2double((int)(((mag >> 3) + (896u << 20)) | (u & 0x80000000u)), (int)(u << 29));
+    }
     const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
     unsigned e = (u >> 23) & 0xffu;
     unsigned m = u & 0x7fffffu;
