@@ -201,7 +201,7 @@ nm_status nm_potential_host(nm_plan_t plan, const void* rho_host, double* phi_ho
 /* Device bytes held by the plan (workspace, excluding the shared spectrum),
  * and the bytes of the cached spectra it uses (each octant in double, float
  * and double-float; for FP32 plans with 2N >= 64 also the float rows over all
- * kx that the paired z-seam reads); for admission control. */
+ * kx that both FP32 z-seams read); for admission control. */
 nm_status nm_workspace_bytes(nm_plan_t plan, size_t* bytes);
 nm_status nm_spectrum_bytes(nm_plan_t plan, size_t* bytes);
 

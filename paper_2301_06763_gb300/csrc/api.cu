@@ -1580,8 +1580,8 @@ nm_status nm_spectrum_bytes(nm_plan_t p, size_t* bytes) {
     size_t b = octant_count(p->N) * per;
     if (p->spec_dbl) b += octant_count(2 * p->N) * per;
     if (p->spec_qdp) b += octant_count(4 * p->N) * per;
-    // float rows over all kx, for the paired FP32 z-seam (P >= 64), and the
-    // float octant with fz fastest, for the three-pass form
+    // float rows over all kx, for the FP32 z-seams (P >= 64), and the float
+    // octant with fz fastest, for the three-pass form
     if (p->fp32 && p->P >= 64) b += (size_t)(p->N + 1) * (p->N + 1) * p->P * sizeof(float);
     if (p->fp32 && p->P >= 64) b += octant_count(p->N) * sizeof(float);
     *bytes = b;
